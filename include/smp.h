@@ -1,0 +1,183 @@
+/*
+ * smp.h -- C ABI of libsmp, a GB300 (sm_103a) implementation of SMP-PCA, the single-pass rank-r approximation of
+ * A^T B from "Single Pass PCA of Matrix Products" (Wu, Bhojanapalli, Sanghavi, Dimakis; arXiv 1610.06656).
+ *
+ * The path (Algorithm 1):
+ *   smp_sketch_begin / smp_sketch_accumulate / smp_sketch_finalize   step 2: At = Pi A, Bt = Pi B, ||A_i||, ||B_j||
+ *   smp_sample                                                       step 3: Omega by Eq. (1)
+ *   smp_estimate                                                     step 4: M~ over Omega by Eq. (2)
+ *   smp_waltmin                                                      step 5: Algorithm 2 (Appendix A)
+ *
+ * Conventions shared by every call:
+ *   - Pointers named *_dev are CUDA device pointers owned by the caller unless stated otherwise. Pointers
+ *     returned by the *_view calls are borrowed from the context and stay valid until smp_destroy (or until the
+ *     next call that rebuilds them, as stated).
+ *   - Every call is issued on the context's stream (the cudaStream_t given to smp_sketch_begin, passed as void*).
+ *     Calls are asynchronous unless stated; smp_sample and smp_waltmin synchronise the stream before returning.
+ *   - Every call returns an smp_status and never aborts the process. smp_last_error gives a one-line reason.
+ *     A kernel that detects a numerical failure records it in a device error word that the next synchronising
+ *     call reports (SMP_ENUMERIC / SMP_ETIMEOUT).
+ *   - Matrices are row-major. A row block holds data rows [row0, row0 + nrows) of A (nrows x n1, leading
+ *     dimension lda elements) and of B (nrows x n2, ldb). Blocks may arrive in any order and any number of
+ *     times per row range is an error the library cannot see (it sums what it is given).
+ *   - Randomness: Pi, the sampling coins, the optional Omega split and the start block of the initial subspace
+ *     iteration come from Philox4x32-10 (Salmon et al., SC'11) with the counter layouts documented with each
+ *     call, so results are a function of (inputs, seeds) only.
+ */
+#ifndef SMP_H
+#define SMP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SMP_OK = 0,
+    SMP_EINVAL = 1,        /* bad argument: null pointer, size out of range, misaligned leading dimension */
+    SMP_ENOMEM = 2,        /* a device allocation failed */
+    SMP_ECUDA = 3,         /* a CUDA runtime call failed (see smp_last_error) */
+    SMP_ESTATE = 4,        /* call out of order (e.g. accumulate after finalize, estimate before sample) */
+    SMP_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+    SMP_ENUMERIC = 6,      /* a factorisation broke down (non-positive pivot) */
+    SMP_EUNSUPPORTED = 7   /* valid request this build does not implement (e.g. dtype/engine pair) */
+} smp_status;
+
+typedef enum {
+    SMP_F32 = 0,           /* row blocks are float */
+    SMP_BF16 = 1,          /* row blocks are bfloat16 */
+    SMP_F64 = 2            /* row blocks are double; the sketch accumulates in double */
+} smp_dtype;
+
+typedef enum {
+    SMP_ENGINE_AUTO = 0,   /* tensor-core sketch where the dtype has one, else SIMT */
+    SMP_ENGINE_SIMT = 1,   /* CUDA-core sketch: FP32 FMA (FP64 for SMP_F64); the exact-arithmetic reference */
+    SMP_ENGINE_TC = 2      /* tcgen05 sketch: TF32 operands for SMP_F32, BF16 operands for SMP_BF16 */
+} smp_engine;
+
+/* smp_waltmin flags */
+#define SMP_SPLIT_OMEGA 1u   /* Algorithm 2 step 3: each sample joins subset floor(u (2T+1)), u its split coin  */
+#define SMP_NO_TRIM     2u   /* skip Algorithm 2 step 6                                                          */
+#define SMP_INIT_GIVEN  4u   /* use the caller's U_init (n1 x r, double) instead of steps 4-6                    */
+#define SMP_FP64_ALS    8u   /* Gram matrices and iterates in double (default: float Gram, double Cholesky)     */
+
+typedef struct {
+    int64_t n1;            /* columns of A (>= 1)                                                             */
+    int64_t n2;            /* columns of B (>= 1); must equal n1 when same_ab                                  */
+    int32_t k;             /* sketch size, 1 <= k <= 1024                                                      */
+    int32_t dtype;         /* smp_dtype of the row blocks                                                      */
+    uint64_t seed;         /* Pi seed: Philox key (seed mod 2^32, seed >> 32)                                  */
+    int32_t same_ab;       /* 1: B is A (PCA, Section 3 Remark 3); B pointers are ignored and Bt aliases At     */
+    int32_t engine;        /* smp_engine                                                                       */
+    int64_t max_rows;      /* largest nrows any accumulate call will pass (sizes scratch); 0 means 65,536      */
+} smp_params;
+
+typedef struct smp_ctx smp_ctx;
+
+/* Create a context and its resident device accumulators (Algorithm 1, step 2: the sketch state At, Bt and the
+ * column sums of squares). stream is a cudaStream_t (NULL = legacy default stream); the context uses the device
+ * current at this call. On success *out owns about 4 * (n1 + n2) * (k + 4) * S bytes of device memory, S the
+ * number of row splits the sketch engine uses (at most 8). Errors: SMP_EINVAL, SMP_ENOMEM, SMP_ECUDA. */
+smp_status smp_sketch_begin(const smp_params* params, void* stream, smp_ctx** out);
+
+/* Add the contribution of data rows [row0, row0 + nrows): At += Pi[:, rows] A_blk, Bt += Pi[:, rows] B_blk and the
+ * squares of every entry to the column sums (Algorithm 1, step 2; Section 2.1 "Step 1"). Pi(a, t) ~ N(0, 1/k) is
+ * never stored: it is generated from Philox counter (t mod 2^32, t >> 32, a / 4, 1) with a Box-Muller map
+ * (words 0,1 -> rows 4g, 4g+1; words 2,3 -> rows 4g+2, 4g+3; u1 = ((x>>8)+1) 2^-24, u2 = (x>>8) 2^-24,
+ * rho = sqrt(-2 ln u1), z = rho cos(2 pi u2), rho sin(2 pi u2), Pi = z / sqrt(k)).
+ * A_blk_dev / B_blk_dev: device, row-major, element type from params.dtype, lda >= n1, ldb >= n2; B ignored when
+ * same_ab. 0 <= nrows <= max_rows; nrows = 0 is a no-op. Asynchronous. Errors: SMP_EINVAL, SMP_ESTATE (after
+ * finalize), SMP_ECUDA. */
+smp_status smp_sketch_accumulate(smp_ctx* ctx, const void* A_blk_dev, int64_t lda, const void* B_blk_dev,
+                                 int64_t ldb, int64_t row0, int64_t nrows);
+
+/* Same as smp_sketch_accumulate but with Pi[:, row0:row0+nrows] supplied by the caller (test hook: Pi = I, or
+ * the oracle's Pi). Pi_blk_dev is k x nrows row-major with leading dimension ldp, element type float (double for
+ * SMP_F64). Always runs the SIMT engine. */
+smp_status smp_sketch_accumulate_pi(smp_ctx* ctx, const void* Pi_blk_dev, int64_t ldp, const void* A_blk_dev,
+                                    int64_t lda, const void* B_blk_dev, int64_t ldb, int64_t row0, int64_t nrows);
+
+/* Start a new single pass on an existing context: clears the accumulators, the finalized sketch and Omega, keeps
+ * every allocation (so a serving loop or a benchmark reuses one context per problem shape). Asynchronous. */
+smp_status smp_sketch_reset(smp_ctx* ctx);
+
+/* Close the single pass: reduce the row-split partials in a fixed order (bitwise reproducible), form
+ * ||A_i||^2 in double, ||A||_F^2 = sum_i ||A_i||^2 summed left to right, ||At_i|| and the rescale factors
+ * (D_A)_ii = ||A_i|| / ||At_i|| (0 when ||At_i|| = 0), the compact form of Eq. (2) (Appendix B). Same for B.
+ * Asynchronous. Errors: SMP_ESTATE (twice), SMP_ECUDA. */
+smp_status smp_sketch_finalize(smp_ctx* ctx);
+
+/* Borrow the finalized sketch (valid until smp_destroy). At_dev: n1 x ldk row-major (row i = sketch column At_i,
+ * k values then padding), Bt_dev: n2 x ldk (== At_dev when same_ab); float, or double for SMP_F64.
+ * sA_dev/sB_dev: ||A_i||^2, ||B_j||^2 (double, device). F_host: {||A||_F^2, ||B||_F^2} copied to the host
+ * (synchronises). Any output pointer may be NULL. Errors: SMP_ESTATE before finalize. */
+smp_status smp_sketch_view(smp_ctx* ctx, const void** At_dev, const void** Bt_dev, int64_t* ldk,
+                           const double** sA_dev, const double** sB_dev, double* F_host);
+
+/* Replace the sketch state with caller data (stage-parity and resume hook); marks the context finalized.
+ * At_dev: n1 x k row-major, Bt_dev: n2 x k (ignored when same_ab), float (double for SMP_F64); sA_dev, sB_dev:
+ * double column sums of squares. Copies; asynchronous. */
+smp_status smp_sketch_import(smp_ctx* ctx, const void* At_dev, const void* Bt_dev, const double* sA_dev,
+                             const double* sB_dev);
+
+/* Draw Omega (Algorithm 1, step 3): (i, j) is kept iff u_ij < q^_ij = min{1, q_ij}, q_ij = alpha_i + beta_j,
+ * alpha_i = m * (||A_i||^2 / ((2 n2) ||A||_F^2)), beta_j = m * (||B_j||^2 / ((2 n1) ||B||_F^2)) (Eq. (1); every
+ * step one IEEE binary64 operation in this order, so given the same norms Omega is bit-identical to any
+ * implementation that follows it). u_ij = ((x0 >> 5) 2^26 + (x1 >> 6)) 2^-53 from Philox counter (i, j, 0, 2) under
+ * key (seed mod 2^32, seed >> 32). m > 0 is the sample budget as a double (no rounding). Builds the context-owned
+ * CSR (row-major canonical order) and CSC views of Omega. Synchronises; *nnz_out receives |Omega|.
+ * Errors: SMP_ESTATE (before finalize), SMP_EINVAL (m <= 0, both Frobenius norms zero), SMP_ENOMEM. */
+smp_status smp_sample(smp_ctx* ctx, double m, uint64_t seed, int64_t* nnz_out);
+
+/* smp_sample with caller-supplied column sums of squares (double device arrays of n1 and n2 entries) in place of
+ * the sketch's: the stage-parity hook for bit-exact Omega. Does not need a finalized sketch. */
+smp_status smp_sample_from_norms(smp_ctx* ctx, const double* sA_dev, const double* sB_dev, double m,
+                                 uint64_t seed, int64_t* nnz_out);
+
+/* Borrow Omega (valid until the next smp_sample* or smp_destroy). CSR: row_ptr[n1+1] (int64), col[nnz] (int32,
+ * increasing within a row), qhat[nnz] (double q^_ij). CSC: col_ptr[n2+1] (int64), csc_row[nnz] (int32,
+ * increasing within a column), csc_pos[nnz] (int64, position of the entry in the CSR arrays). Any output may be
+ * NULL. Errors: SMP_ESTATE before sampling. */
+smp_status smp_omega_view(const smp_ctx* ctx, int64_t* nnz, const int64_t** row_ptr, const int32_t** col,
+                          const double** qhat, const int64_t** col_ptr, const int32_t** csc_row,
+                          const int64_t** csc_pos);
+
+/* M~(i, j) = ||A_i|| ||B_j|| <At_i, Bt_j> / (||At_i|| ||Bt_j||) for every (i, j) in Omega, in CSR order
+ * (Algorithm 1, step 4; Eq. (2)); 0 when a sketch column is zero. vals_dev: caller device buffer of nnz floats
+ * (doubles for SMP_F64). Asynchronous. Errors: SMP_ESTATE (before sampling). */
+smp_status smp_estimate(smp_ctx* ctx, void* vals_dev);
+
+/* WAltMin(P_Omega(M~), Omega, r, q^, T) (Algorithm 2) followed by the canonical form of U^ V^T:
+ * w_ij = 1/q^_ij; U0 = top-r left singular subspace of R_Omega0(M~) by block subspace iteration (Philox start
+ * block, counter (i, 0, c/4, 4) under key seed) with a Rayleigh-Ritz step; trim: row i of U0 is zeroed when
+ * ||U0^i|| > 8 sqrt(r) ||A_i|| / ||A||_F; then T rounds of the weighted least-squares V- and U-updates, each row
+ * solving (G + lambda I) x = b with G = sum w f f^T, b = sum w M~ f, lambda = 1e-10 tr(G)/r (x = 0 when tr(G) = 0),
+ * by a double-precision Cholesky. Finally QR(U^) = Qu Ru, QR(V^) = Qv Rv, SVD(Ru Rv^T) = W S Z^T, U = Qu W,
+ * V = Qv Z, the largest-magnitude entry of each U column made positive.
+ * vals_dev: P_Omega(M~) in CSR order (float; double for SMP_F64), e.g. from smp_estimate. 1 <= r <= 32,
+ * r <= min(n1, n2); T >= 0. flags: SMP_* above. seed: split and start-block key. U_init_dev: n1 x r double,
+ * read only with SMP_INIT_GIVEN. Outputs (device, double, row-major): U_dev n1 x r, S_dev r, V_dev n2 x r.
+ * Synchronises. Errors: SMP_ESTATE, SMP_EINVAL, SMP_ENUMERIC, SMP_ENOMEM. */
+smp_status smp_waltmin(smp_ctx* ctx, const void* vals_dev, int32_t r, int32_t T, uint32_t flags, uint64_t seed,
+                       const double* U_init_dev, double* U_dev, double* S_dev, double* V_dev);
+
+/* Block until the context's stream is idle and report any device-side error word. */
+smp_status smp_sync(smp_ctx* ctx);
+
+/* Free the context and everything it owns. NULL is a no-op. */
+smp_status smp_destroy(smp_ctx* ctx);
+
+/* One-line description of the last failure on ctx (or of the last failed smp_sketch_begin when ctx is NULL). */
+const char* smp_last_error(const smp_ctx* ctx);
+
+/* Name of a status code. */
+const char* smp_status_string(smp_status s);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int32_t smp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMP_H */

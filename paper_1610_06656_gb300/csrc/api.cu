@@ -1,0 +1,312 @@
+// libsmp C ABI: argument checks, context lifecycle, call ordering and error reporting. Every compute step runs in
+// the kernels of sketch*.cu, sample.cu, estimate.cu and waltmin.cu; this file only validates and dispatches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace {
+thread_local std::string g_begin_error;
+}
+
+namespace smp {
+
+smp_status fail(smp_ctx* c, smp_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_begin_error = msg;
+    return s;
+}
+
+smp_status check_cuda(smp_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return SMP_OK;
+    cudaGetLastError();
+    return fail(c, e == cudaErrorMemoryAllocation ? SMP_ENOMEM : SMP_ECUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+smp_status read_device_error(smp_ctx* c) {
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return check_cuda(c, e, "reading the device error word");
+    if (h == 0) return SMP_OK;
+    cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream);
+    if (h & DEVERR_TIMEOUT) return fail(c, SMP_ETIMEOUT, "a bounded device-side wait gave up");
+    if (h & DEVERR_NUMERIC) return fail(c, SMP_ENUMERIC, "a Cholesky pivot was not positive");
+    return fail(c, SMP_ECUDA, "a kernel index check failed");
+}
+
+}  // namespace smp
+
+using namespace smp;
+
+namespace {
+
+void free_ctx(smp_ctx* c) {
+    void* ptrs[] = {c->part,   c->nsq,    c->sk,      c->s_all,   c->D_all,   c->F,     c->row_ptr, c->col_ptr,
+                    c->col,    c->qhat,   c->csc_row, c->csc_pos, c->alpha,   c->beta,  c->mask,    c->wpre,
+                    c->row_cnt, c->col_cnt, c->dev_err, c->tc_ws};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete c;
+}
+
+bool elem_size(int dtype, size_t* sz) {
+    switch (dtype) {
+        case SMP_F32: *sz = 4; return true;
+        case SMP_BF16: *sz = 2; return true;
+        case SMP_F64: *sz = 8; return true;
+    }
+    return false;
+}
+
+smp_status check_block(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t nrows) {
+    if (!c) return fail(nullptr, SMP_EINVAL, "null context");
+    if (c->finalized) return fail(c, SMP_ESTATE, "accumulate after finalize");
+    if (nrows < 0 || nrows > c->max_rows) return fail(c, SMP_EINVAL, "nrows out of [0, max_rows]");
+    if (nrows == 0) return SMP_OK;
+    if (!A || lda < c->p.n1) return fail(c, SMP_EINVAL, "A_blk is null or lda < n1");
+    if (!c->p.same_ab && (!B || ldb < c->p.n2)) return fail(c, SMP_EINVAL, "B_blk is null or ldb < n2");
+    return SMP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+smp_status smp_sketch_begin(const smp_params* params, void* stream, smp_ctx** out) {
+    if (!params || !out) return fail(nullptr, SMP_EINVAL, "null params or out");
+    *out = nullptr;
+    const smp_params& p = *params;
+    size_t esz = 0;
+    if (!elem_size(p.dtype, &esz)) return fail(nullptr, SMP_EINVAL, "unknown dtype");
+    if (p.n1 < 1 || p.n2 < 1 || p.n1 > (int64_t)1 << 30 || p.n2 > (int64_t)1 << 30)
+        return fail(nullptr, SMP_EINVAL, "n1, n2 must be in [1, 2^30]");
+    if (p.same_ab && p.n1 != p.n2) return fail(nullptr, SMP_EINVAL, "same_ab needs n1 == n2");
+    if (p.k < 1 || p.k > 1024) return fail(nullptr, SMP_EINVAL, "k must be in [1, 1024]");
+    if (p.engine < SMP_ENGINE_AUTO || p.engine > SMP_ENGINE_TC) return fail(nullptr, SMP_EINVAL, "unknown engine");
+    if (p.max_rows < 0) return fail(nullptr, SMP_EINVAL, "max_rows < 0");
+    smp_ctx* c = new (std::nothrow) smp_ctx();
+    if (!c) return fail(nullptr, SMP_ENOMEM, "host allocation");
+    c->p = p;
+    c->stream = (cudaStream_t)stream;
+    c->max_rows = p.max_rows ? p.max_rows : 65536;
+    c->acc_bytes = p.dtype == SMP_F64 ? 8 : 4;
+    c->ntot = p.same_ab ? p.n1 : p.n1 + p.n2;
+    c->ldk = round_up(p.k, 4);
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        smp_status s = check_cuda(nullptr, e, "smp_sketch_begin: device query");
+        delete c;
+        return s;
+    }
+    c->splits = 8;
+    const size_t acc = (size_t)c->acc_bytes;
+    const int64_t n1 = p.n1, n2 = p.n2;
+    bool ok = true;
+    auto alloc = [&](void** ptr, size_t bytes) {
+        if (!ok) return;
+        if (cudaMalloc(ptr, std::max<size_t>(bytes, 16)) != cudaSuccess) ok = false;
+    };
+    alloc(&c->part, (size_t)c->splits * c->ntot * c->ldk * acc);
+    alloc((void**)&c->nsq, (size_t)c->splits * c->ntot * 8);
+    alloc(&c->sk, (size_t)c->ntot * c->ldk * acc);
+    alloc((void**)&c->s_all, (size_t)c->ntot * 8);
+    alloc((void**)&c->D_all, (size_t)c->ntot * 8);
+    alloc((void**)&c->F, 16);
+    alloc((void**)&c->row_ptr, (size_t)(n1 + 1) * 8);
+    alloc((void**)&c->col_ptr, (size_t)(n2 + 1) * 8);
+    alloc((void**)&c->alpha, (size_t)n1 * 8);
+    alloc((void**)&c->beta, (size_t)n2 * 8);
+    alloc((void**)&c->row_cnt, (size_t)n1 * 4);
+    alloc((void**)&c->col_cnt, (size_t)n2 * 4);
+    alloc((void**)&c->dev_err, sizeof(int));
+    if (!ok) {
+        cudaGetLastError();
+        free_ctx(c);
+        return fail(nullptr, SMP_ENOMEM, "smp_sketch_begin: device allocation failed");
+    }
+    cudaStream_t st = c->stream;
+    e = cudaMemsetAsync(c->part, 0, (size_t)c->splits * c->ntot * c->ldk * acc, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->nsq, 0, (size_t)c->splits * c->ntot * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->dev_err, 0, sizeof(int), st);
+    if (e != cudaSuccess) {
+        smp_status s = check_cuda(nullptr, e, "smp_sketch_begin: clearing accumulators");
+        free_ctx(c);
+        return s;
+    }
+    *out = c;
+    return SMP_OK;
+}
+
+smp_status smp_sketch_accumulate(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t row0,
+                                 int64_t nrows) {
+    smp_status s = check_block(c, A, lda, B, ldb, nrows);
+    if (s != SMP_OK || nrows == 0) return s;
+    if (row0 < 0) return fail(c, SMP_EINVAL, "row0 < 0");
+    const bool want_tc = c->p.engine == SMP_ENGINE_TC || (c->p.engine == SMP_ENGINE_AUTO && tc_supported(c));
+    if (c->p.engine == SMP_ENGINE_TC && !tc_supported(c))
+        return fail(c, SMP_EUNSUPPORTED, "the tensor-core sketch does not support this dtype / shape");
+    cudaError_t e = want_tc ? launch_sketch_tc(c, A, lda, B, ldb, row0, nrows)
+                            : launch_sketch_simt(c, A, lda, B, ldb, row0, nrows, nullptr, 0);
+    return check_cuda(c, e, "smp_sketch_accumulate");
+}
+
+smp_status smp_sketch_accumulate_pi(smp_ctx* c, const void* Pi, int64_t ldp, const void* A, int64_t lda,
+                                    const void* B, int64_t ldb, int64_t row0, int64_t nrows) {
+    smp_status s = check_block(c, A, lda, B, ldb, nrows);
+    if (s != SMP_OK || nrows == 0) return s;
+    if (!Pi || ldp < nrows) return fail(c, SMP_EINVAL, "Pi_blk is null or ldp < nrows");
+    return check_cuda(c, launch_sketch_simt(c, A, lda, B, ldb, row0, nrows, Pi, ldp), "smp_sketch_accumulate_pi");
+}
+
+smp_status smp_sketch_reset(smp_ctx* c) {
+    if (!c) return fail(nullptr, SMP_EINVAL, "null context");
+    cudaError_t e = cudaMemsetAsync(c->part, 0, (size_t)c->splits * c->ntot * c->ldk * c->acc_bytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->nsq, 0, (size_t)c->splits * c->ntot * 8, c->stream);
+    if (e != cudaSuccess) return check_cuda(c, e, "smp_sketch_reset");
+    c->finalized = false;
+    c->sampled = false;
+    c->nnz = 0;
+    return SMP_OK;
+}
+
+smp_status smp_sketch_finalize(smp_ctx* c) {
+    if (!c) return fail(nullptr, SMP_EINVAL, "null context");
+    if (c->finalized) return fail(c, SMP_ESTATE, "finalize called twice");
+    smp_status s = check_cuda(c, launch_finalize(c), "smp_sketch_finalize");
+    if (s == SMP_OK) c->finalized = true;
+    return s;
+}
+
+smp_status smp_sketch_view(smp_ctx* c, const void** At, const void** Bt, int64_t* ldk, const double** sA,
+                           const double** sB, double* F_host) {
+    if (!c) return fail(nullptr, SMP_EINVAL, "null context");
+    if (!c->finalized) return fail(c, SMP_ESTATE, "sketch not finalized");
+    const char* base = (const char*)c->sk;
+    if (At) *At = base;
+    if (Bt) *Bt = c->p.same_ab ? base : base + (size_t)c->p.n1 * c->ldk * c->acc_bytes;
+    if (ldk) *ldk = c->ldk;
+    if (sA) *sA = c->s_all;
+    if (sB) *sB = c->p.same_ab ? c->s_all : c->s_all + c->p.n1;
+    if (F_host) {
+        cudaError_t e = cudaMemcpyAsync(F_host, c->F, 16, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return check_cuda(c, e, "smp_sketch_view");
+    }
+    return SMP_OK;
+}
+
+smp_status smp_sketch_import(smp_ctx* c, const void* At, const void* Bt, const double* sA, const double* sB) {
+    if (!c) return fail(nullptr, SMP_EINVAL, "null context");
+    if (!At || !sA || (!c->p.same_ab && (!Bt || !sB))) return fail(c, SMP_EINVAL, "null sketch or norms");
+    smp_status s = check_cuda(c, launch_import(c, At, Bt, sA, sB), "smp_sketch_import");
+    if (s == SMP_OK) c->finalized = true;
+    return s;
+}
+
+smp_status smp_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out) {
+    if (!c) return fail(nullptr, SMP_EINVAL, "null context");
+    if (!c->finalized) return fail(c, SMP_ESTATE, "smp_sample before finalize");
+    if (!(m > 0.0)) return fail(c, SMP_EINVAL, "m must be > 0");
+    double F[2];
+    cudaError_t e = cudaMemcpyAsync(F, c->F, 16, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return check_cuda(c, e, "smp_sample");
+    if (!(F[0] > 0.0) && !(F[1] > 0.0)) return fail(c, SMP_EINVAL, "both Frobenius norms are zero");
+    return run_sample(c, m, seed, nnz_out);
+}
+
+smp_status smp_sample_from_norms(smp_ctx* c, const double* sA, const double* sB, double m, uint64_t seed,
+                                 int64_t* nnz_out) {
+    if (!c) return fail(nullptr, SMP_EINVAL, "null context");
+    if (!sA || (!c->p.same_ab && !sB)) return fail(c, SMP_EINVAL, "null norms");
+    if (!(m > 0.0)) return fail(c, SMP_EINVAL, "m must be > 0");
+    cudaError_t e = cudaMemcpyAsync(c->s_all, sA, (size_t)c->p.n1 * 8, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess && !c->p.same_ab)
+        e = cudaMemcpyAsync(c->s_all + c->p.n1, sB, (size_t)c->p.n2 * 8, cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return check_cuda(c, e, "smp_sample_from_norms");
+    smp_status s = run_sample(c, m, seed, nnz_out);
+    if (s != SMP_OK) return s;
+    double F[2];
+    e = cudaMemcpy(F, c->F, 16, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return check_cuda(c, e, "smp_sample_from_norms");
+    if (!(F[0] > 0.0) && !(F[1] > 0.0)) return fail(c, SMP_EINVAL, "both Frobenius norms are zero");
+    return SMP_OK;
+}
+
+smp_status smp_omega_view(const smp_ctx* c, int64_t* nnz, const int64_t** row_ptr, const int32_t** col,
+                          const double** qhat, const int64_t** col_ptr, const int32_t** csc_row,
+                          const int64_t** csc_pos) {
+    if (!c) return fail(nullptr, SMP_EINVAL, "null context");
+    if (!c->sampled) return fail(const_cast<smp_ctx*>(c), SMP_ESTATE, "Omega not drawn yet");
+    if (nnz) *nnz = c->nnz;
+    if (row_ptr) *row_ptr = c->row_ptr;
+    if (col) *col = c->col;
+    if (qhat) *qhat = c->qhat;
+    if (col_ptr) *col_ptr = c->col_ptr;
+    if (csc_row) *csc_row = c->csc_row;
+    if (csc_pos) *csc_pos = c->csc_pos;
+    return SMP_OK;
+}
+
+smp_status smp_estimate(smp_ctx* c, void* vals) {
+    if (!c) return fail(nullptr, SMP_EINVAL, "null context");
+    if (!c->sampled || !c->finalized) return fail(c, SMP_ESTATE, "smp_estimate needs a finalized sketch and Omega");
+    if (!vals && c->nnz > 0) return fail(c, SMP_EINVAL, "null vals");
+    return check_cuda(c, launch_estimate(c, vals), "smp_estimate");
+}
+
+smp_status smp_waltmin(smp_ctx* c, const void* vals, int32_t r, int32_t T, uint32_t flags, uint64_t seed,
+                       const double* U_init, double* U, double* S, double* V) {
+    if (!c) return fail(nullptr, SMP_EINVAL, "null context");
+    if (!c->sampled) return fail(c, SMP_ESTATE, "smp_waltmin before smp_sample");
+    if (r < 1 || r > 32 || r > c->p.n1 || r > c->p.n2) return fail(c, SMP_EINVAL, "r out of [1, min(32, n1, n2)]");
+    if (T < 0 || T > 127) return fail(c, SMP_EINVAL, "T out of [0, 127]");
+    if (flags & ~(SMP_SPLIT_OMEGA | SMP_NO_TRIM | SMP_INIT_GIVEN | SMP_FP64_ALS))
+        return fail(c, SMP_EINVAL, "unknown flag");
+    if ((flags & SMP_INIT_GIVEN) && !U_init) return fail(c, SMP_EINVAL, "SMP_INIT_GIVEN without U_init");
+    if (!U || !S || !V || (!vals && c->nnz > 0)) return fail(c, SMP_EINVAL, "null output or vals");
+    return run_waltmin(c, vals, r, T, flags, seed, U_init, U, S, V);
+}
+
+smp_status smp_sync(smp_ctx* c) {
+    if (!c) return fail(nullptr, SMP_EINVAL, "null context");
+    smp_status s = check_cuda(c, cudaStreamSynchronize(c->stream), "smp_sync");
+    if (s != SMP_OK) return s;
+    return read_device_error(c);
+}
+
+smp_status smp_destroy(smp_ctx* c) {
+    if (!c) return SMP_OK;
+    cudaStreamSynchronize(c->stream);
+    free_ctx(c);
+    return SMP_OK;
+}
+
+const char* smp_last_error(const smp_ctx* c) { return c ? c->err.c_str() : g_begin_error.c_str(); }
+
+const char* smp_status_string(smp_status s) {
+    switch (s) {
+        case SMP_OK: return "SMP_OK";
+        case SMP_EINVAL: return "SMP_EINVAL";
+        case SMP_ENOMEM: return "SMP_ENOMEM";
+        case SMP_ECUDA: return "SMP_ECUDA";
+        case SMP_ESTATE: return "SMP_ESTATE";
+        case SMP_ETIMEOUT: return "SMP_ETIMEOUT";
+        case SMP_ENUMERIC: return "SMP_ENUMERIC";
+        case SMP_EUNSUPPORTED: return "SMP_EUNSUPPORTED";
+    }
+    return "SMP_UNKNOWN";
+}
+
+int32_t smp_version(void) { return 100; }
+
+}  // extern "C"

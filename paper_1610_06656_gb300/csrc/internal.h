@@ -1,0 +1,79 @@
+// Host-side internals of libsmp: the context object and the kernel launchers each translation unit exports.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/smp.h"
+
+struct smp_ctx {
+    smp_params p{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int sm_count = 0;
+    int acc_bytes = 4;              // 4: float sketch state, 8: double (SMP_F64)
+    bool finalized = false;
+    bool sampled = false;
+    int64_t ntot = 0;               // n1 + n2 (n1 when same_ab)
+    int64_t ldk = 0;                // k rounded up to a multiple of 4
+    int64_t max_rows = 0;
+    int splits = 1;                 // row splits of the sketch partials
+    void* part = nullptr;           // [splits][ntot][ldk] partial sketches (acc type)
+    double* nsq = nullptr;          // [splits][ntot] partial column sums of squares
+    void* sk = nullptr;             // [ntot][ldk] finalized sketch (row c = sketch column c)
+    double* s_all = nullptr;        // [ntot] column sums of squares (A columns, then B columns)
+    double* D_all = nullptr;        // [ntot] rescale factors ||X_c|| / ||Xt_c||
+    double* F = nullptr;            // [2] Frobenius squares (device)
+    // Omega
+    int64_t nnz = 0, cap = 0;
+    int64_t* row_ptr = nullptr;     // [n1 + 1]
+    int64_t* col_ptr = nullptr;     // [n2 + 1]
+    int32_t* col = nullptr;         // [cap]
+    double* qhat = nullptr;         // [cap]
+    int32_t* csc_row = nullptr;     // [cap]
+    int64_t* csc_pos = nullptr;     // [cap]
+    double* alpha = nullptr;        // [n1]
+    double* beta = nullptr;         // [n2]
+    uint32_t* mask = nullptr;       // [n1][W] keep bits, W = ceil(n2 / 32)
+    int32_t* wpre = nullptr;        // [n1][W] set bits of the row before each word
+    int32_t* row_cnt = nullptr;     // [n1]
+    int32_t* col_cnt = nullptr;     // [n2]
+    int64_t mask_words = 0;
+    int* dev_err = nullptr;         // device error word
+    void* tc_ws = nullptr;          // tensor-core engine workspace
+    size_t tc_ws_bytes = 0;
+    std::string err;
+};
+
+namespace smp {
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// sketch.cu
+cudaError_t launch_sketch_simt(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t row0,
+                               int64_t nrows, const void* Pi, int64_t ldp);
+cudaError_t launch_finalize(smp_ctx* c);
+cudaError_t launch_import(smp_ctx* c, const void* At, const void* Bt, const double* sA, const double* sB);
+
+// sketch_tc.cu
+bool tc_supported(const smp_ctx* c);
+cudaError_t launch_sketch_tc(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t row0,
+                             int64_t nrows);
+
+// sample.cu
+smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out);
+
+// estimate.cu
+cudaError_t launch_estimate(smp_ctx* c, void* vals);
+
+// waltmin.cu
+smp_status run_waltmin(smp_ctx* c, const void* vals, int r, int T, uint32_t flags, uint64_t seed,
+                       const double* U_init, double* U, double* S, double* V);
+
+// api.cu
+smp_status fail(smp_ctx* c, smp_status s, const std::string& msg);
+smp_status check_cuda(smp_ctx* c, cudaError_t e, const char* what);
+smp_status read_device_error(smp_ctx* c);
+
+}  // namespace smp

@@ -1,0 +1,279 @@
+// Biased Bernoulli sampling of Omega (Algorithm 1, step 3; Eq. (1)).
+//
+// The coin of (i, j) is u_ij < q^_ij with q_ij = alpha_i + beta_j, alpha_i = m * (s_A,i / ((2 n2) F_A)),
+// beta_j = m * (s_B,j / ((2 n1) F_B)), F = sum of the column sums of squares left to right. Every floating-point
+// step is a single round-to-nearest binary64 operation written with the _rn intrinsics (never contracted), so two
+// implementations that follow the same order draw the same Omega bit for bit.
+//
+// Pipeline: terms (alpha, beta, F) -> coin words (one warp per 32 columns of a row: ballot of the 32 coins,
+// popcount per word, column counts) -> per-row prefix over words -> scans to row_ptr / col_ptr -> CSR fill from
+// the bit words -> CSC fill (one CTA per column, block scan over rows, CSR position from the word prefix).
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace smp {
+namespace {
+
+__global__ void terms_kernel(const double* __restrict__ s_all, int64_t n1, int64_t n2, int same_ab, double m,
+                             double* F, double* alpha, double* beta) {
+    __shared__ double fab[2];
+    if (threadIdx.x == 0) {
+        double fa = 0.0;
+        for (int64_t i = 0; i < n1; ++i) fa = __dadd_rn(fa, s_all[i]);
+        double fb = fa;
+        if (!same_ab) {
+            fb = 0.0;
+            for (int64_t j = 0; j < n2; ++j) fb = __dadd_rn(fb, s_all[n1 + j]);
+        }
+        fab[0] = fa;
+        fab[1] = fb;
+        F[0] = fa;
+        F[1] = fb;
+    }
+    __syncthreads();
+    const double fa = fab[0], fb = fab[1];
+    const double* sB = same_ab ? s_all : s_all + n1;
+    const double da = __dmul_rn((double)(2 * n2), fa);
+    const double db = __dmul_rn((double)(2 * n1), fb);
+    for (int64_t i = threadIdx.x; i < n1; i += blockDim.x)
+        alpha[i] = fa > 0.0 ? __dmul_rn(m, __ddiv_rn(s_all[i], da)) : 0.0;
+    for (int64_t j = threadIdx.x; j < n2; j += blockDim.x)
+        beta[j] = fb > 0.0 ? __dmul_rn(m, __ddiv_rn(sB[j], db)) : 0.0;
+}
+
+__device__ __forceinline__ double qhat_of(double a, double b) {
+    const double q = __dadd_rn(a, b);
+    return q < 1.0 ? q : 1.0;
+}
+
+// One warp per (row i, word w): lane l flips the coin of column 32 w + l.
+__global__ void coin_kernel(const double* __restrict__ alpha, const double* __restrict__ beta, int64_t n1,
+                            int64_t n2, int64_t W, uint32_t k0, uint32_t k1, uint32_t* mask, int32_t* col_cnt) {
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n1 * W) return;
+    const int64_t i = warp / W, w = warp - i * W;
+    const int64_t j = w * 32 + lane;
+    bool keep = false;
+    if (j < n2) {
+        const double u = coin((uint32_t)i, (uint32_t)j, TAG_SAMPLE, k0, k1);
+        keep = u < qhat_of(alpha[i], beta[j]);
+    }
+    const uint32_t bits = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) mask[warp] = bits;
+    if (keep) atomicAdd(&col_cnt[j], 1);
+}
+
+// Per row: exclusive prefix of the word popcounts and the row total (one CTA per row, sequential in chunks).
+__global__ void row_prefix_kernel(const uint32_t* __restrict__ mask, int64_t n1, int64_t W, int32_t* wpre,
+                                  int32_t* row_cnt) {
+    __shared__ int32_t wsum[32];
+    __shared__ int32_t carry;
+    const int64_t i = blockIdx.x;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < W; base += blockDim.x) {
+        const int64_t w = base + threadIdx.x;
+        const int32_t c = w < W ? __popc(mask[i * W + w]) : 0;
+        // block exclusive scan of c
+        int32_t x = c;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int32_t v = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            wsum[lane] = v;
+        }
+        __syncthreads();
+        const int32_t excl = x - c + (wid ? wsum[wid - 1] : 0) + carry;
+        if (w < W) wpre[i * W + w] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + c;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) row_cnt[i] = carry;
+}
+
+// Exclusive scan of n int32 counts into int64 offsets (out has n + 1 entries). One CTA, chunked, fixed order.
+__global__ void scan_kernel(const int32_t* __restrict__ cnt, int64_t n, int64_t* out) {
+    __shared__ int64_t wsum[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int64_t base = 0; base < n; base += blockDim.x) {
+        const int64_t idx = base + threadIdx.x;
+        const int64_t c = idx < n ? (int64_t)cnt[idx] : 0;
+        int64_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int64_t v = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            wsum[lane] = v;
+        }
+        __syncthreads();
+        const int64_t excl = x - c + (wid ? wsum[wid - 1] : 0) + carry;
+        if (idx < n) out[idx] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + c;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
+
+// CSR fill: one warp per word; kept lanes write their column and q^ at row_ptr + word prefix + lanes below.
+__global__ void fill_csr_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ wpre,
+                                const int64_t* __restrict__ row_ptr, const double* __restrict__ alpha,
+                                const double* __restrict__ beta, int64_t n1, int64_t n2, int64_t W, int32_t* col,
+                                double* qhat) {
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n1 * W) return;
+    const uint32_t bits = mask[warp];
+    if (!((bits >> lane) & 1u)) return;
+    const int64_t i = warp / W, w = warp - i * W;
+    const int64_t j = w * 32 + lane;
+    const int64_t pos = row_ptr[i] + wpre[warp] + __popc(bits & ((1u << lane) - 1u));
+    col[pos] = (int32_t)j;
+    qhat[pos] = qhat_of(alpha[i], beta[j]);
+}
+
+// CSC fill: one CTA per column j; block scan over rows keeps rows in increasing order.
+__global__ void fill_csc_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ wpre,
+                                const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ col_ptr,
+                                int64_t n1, int64_t W, int32_t* csc_row, int64_t* csc_pos) {
+    __shared__ int32_t wsum[32];
+    __shared__ int64_t carry;
+    const int64_t j = blockIdx.x;
+    const int64_t w = j >> 5;
+    const int b = (int)(j & 31);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = col_ptr[j];
+    __syncthreads();
+    for (int64_t base = 0; base < n1; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        uint32_t bits = 0;
+        int32_t keep = 0;
+        if (i < n1) {
+            bits = mask[i * W + w];
+            keep = (bits >> b) & 1u;
+        }
+        int32_t x = keep;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int32_t v = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            wsum[lane] = v;
+        }
+        __syncthreads();
+        const int32_t excl = x - keep + (wid ? wsum[wid - 1] : 0);
+        if (keep) {
+            const int64_t p = carry + excl;
+            csc_row[p] = (int32_t)i;
+            csc_pos[p] = row_ptr[i] + wpre[i * W + w] + __popc(bits & ((1u << b) - 1u));
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += excl + keep;
+        __syncthreads();
+    }
+}
+
+template <typename T>
+cudaError_t ensure(T*& p, int64_t& have, int64_t need) {
+    if (have >= need && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    have = 0;
+    cudaError_t e = cudaMalloc((void**)&p, (size_t)std::max<int64_t>(need, 1) * sizeof(T));
+    if (e == cudaSuccess) have = need;
+    return e;
+}
+
+}  // namespace
+
+smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out) {
+    const int64_t n1 = c->p.n1, n2 = c->p.n2;
+    const int64_t W = (n2 + 31) / 32;
+    cudaStream_t st = c->stream;
+    if (c->mask_words < n1 * W) {
+        if (c->mask) cudaFree(c->mask);
+        if (c->wpre) cudaFree(c->wpre);
+        c->mask = nullptr;
+        c->wpre = nullptr;
+        c->mask_words = 0;
+        if (cudaMalloc((void**)&c->mask, (size_t)(n1 * W) * 4) != cudaSuccess ||
+            cudaMalloc((void**)&c->wpre, (size_t)(n1 * W) * 4) != cudaSuccess)
+            return fail(c, SMP_ENOMEM, "smp_sample: cannot allocate the coin bit words");
+        c->mask_words = n1 * W;
+    }
+    cudaError_t e;
+    terms_kernel<<<1, 256, 0, st>>>(c->s_all, n1, n2, c->p.same_ab, m, c->F, c->alpha, c->beta);
+    if ((e = cudaMemsetAsync(c->col_cnt, 0, (size_t)n2 * 4, st)) != cudaSuccess) return check_cuda(c, e, "memset");
+    const int64_t warps = n1 * W;
+    const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
+    coin_kernel<<<blocks, 256, 0, st>>>(c->alpha, c->beta, n1, n2, W, (uint32_t)seed, (uint32_t)(seed >> 32),
+                                        c->mask, c->col_cnt);
+    row_prefix_kernel<<<(unsigned)n1, 256, 0, st>>>(c->mask, n1, W, c->wpre, c->row_cnt);
+    scan_kernel<<<1, 1024, 0, st>>>(c->row_cnt, n1, c->row_ptr);
+    scan_kernel<<<1, 1024, 0, st>>>(c->col_cnt, n2, c->col_ptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return check_cuda(c, e, "smp_sample count kernels");
+    int64_t nnz = 0;
+    if ((e = cudaMemcpyAsync(&nnz, c->row_ptr + n1, sizeof(int64_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return check_cuda(c, e, "smp_sample nnz copy");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return check_cuda(c, e, "smp_sample sync");
+    if (nnz > c->cap) {
+        int64_t have = c->cap, h2 = c->cap, h3 = c->cap, h4 = c->cap;
+        const int64_t want = nnz + nnz / 8 + 1024;
+        if (ensure(c->col, have, want) != cudaSuccess || ensure(c->qhat, h2, want) != cudaSuccess ||
+            ensure(c->csc_row, h3, want) != cudaSuccess || ensure(c->csc_pos, h4, want) != cudaSuccess)
+            return fail(c, SMP_ENOMEM, "smp_sample: cannot allocate Omega");
+        c->cap = want;
+    }
+    if (nnz > 0) {
+        fill_csr_kernel<<<blocks, 256, 0, st>>>(c->mask, c->wpre, c->row_ptr, c->alpha, c->beta, n1, n2, W, c->col,
+                                                c->qhat);
+        fill_csc_kernel<<<(unsigned)n2, 256, 0, st>>>(c->mask, c->wpre, c->row_ptr, c->col_ptr, n1, W, c->csc_row,
+                                                      c->csc_pos);
+        if ((e = cudaGetLastError()) != cudaSuccess) return check_cuda(c, e, "smp_sample fill kernels");
+    }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return check_cuda(c, e, "smp_sample fill sync");
+    c->nnz = nnz;
+    c->sampled = true;
+    if (nnz_out) *nnz_out = nnz;
+    return SMP_OK;
+}
+
+}  // namespace smp
