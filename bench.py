@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Throughput of SMP-PCA (Algorithm 1) on one GB300 per rank, through libsmp's C ABI.
+
+Workload (default "scale"): A, B in R^{1,000,000 x 2,000} FP32 (16 GB, resident in HBM, larger than L2 so no
+flush is needed), low rank 20 + noise 0.1, column scales (j+1)^-0.5; k = 500, r = 10, T = 10,
+m = 4 n r ln n; rows stream through smp_sketch_accumulate in 65,536-row blocks. One step = one full solve:
+sketch (16 blocks) + finalize + sample + estimate + WAltMin + canonical form.
+
+Prints one JSON line (rank 0). value = solves per second over all ranks (each rank solves its own instance:
+weak scaling, no data-path collective). `roofline` describes the sketch kernel (the dominant one), `e2e` the same
+metric with host-resident inputs copied in every step, `cpu_baseline` the CPU oracle on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--engine auto|simt|tc]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sketch GB/s vs HBM peak; end-to-end solves/s & p99 at fixed spectral error"
+WORKLOADS = {
+    "scale": dict(d=1_000_000, n1=2000, n2=2000, L=20, sigma=0.1, alpha=0.5, k=500, r=10, T=10, block=65536),
+    "tiny": dict(d=2000, n1=200, n2=200, L=10, sigma=0.1, alpha=0.5, k=100, r=5, T=10, block=65536),
+}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_sample(w, seed_in, rows=16384):
+    """Time the CPU oracle on a bounded sample of the workload: the single pass over `rows` of the d rows (scaled
+    by d / rows: the pass is linear in d) plus sampling, estimation and WAltMin at full n (independent of d)."""
+    import numpy as np
+
+    from oracle import smp as O
+    from paper_1610_06656_gb300 import synth
+    A, B = synth.lowrank_plus_noise(rows, w["n1"], w["n2"], w["L"], w["sigma"], w["alpha"], seed=seed_in,
+                                    dtype=np.float32)
+    m = O.default_m(w["n1"], w["n2"], w["r"])
+    t0 = time.perf_counter()
+    st = O.sketch(A, B, w["k"], 1, block_rows=min(rows, w["block"]))
+    t1 = time.perf_counter()
+    rws, cls, qh = O.sample_omega(st.sA, st.sB, m, 2)
+    vals = O.estimate(rws, cls, st.At, st.Bt, st.sA, st.sB)
+    Uh, Vh = O.waltmin(w["n1"], w["n2"], rws, cls, vals, qh, w["r"], w["T"], st.sA)
+    O.canonical(Uh, Vh)
+    t2 = time.perf_counter()
+    per_solve = (t1 - t0) * (w["d"] / rows) + (t2 - t1)
+    return per_solve, t2 - t0
+
+
+def run_reference(args, w):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    cores = len(os.sched_getaffinity(0))
+    rows = 16384 if args.workload == "scale" else w["d"]
+    for _ in range(args.warmup):
+        cpu_oracle_sample(w, 1001, rows)
+    per = []
+    for _ in range(args.steps):
+        p, _ = cpu_oracle_sample(w, 1001, rows)
+        per.append(p)
+    value = len(per) / sum(per)
+    sample = ("single pass over %d of %d rows (time scaled by d/rows) + sampling, estimate, WAltMin at n=%d"
+              % (rows, w["d"], w["n1"]))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(per) / len(per),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, **{k: w[k] for k in ("d", "n1", "n2", "k", "r", "T")},
+                       "block_rows": w["block"], "oracle": "CPU binary64 (numpy/LAPACK)"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def spectral_error(torch, A, B, U, S, V, block=65536):
+    """||A^T B - U S V^T||_2 / ||A^T B||_2 with A^T B accumulated blockwise (FP32 products, no TF32, summed in
+    binary64). Evaluation only: torch / cuSOLVER compute the norm, not the path."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    M = torch.zeros(A.shape[1], B.shape[1], dtype=torch.float64, device=A.device)
+    for r0 in range(0, A.shape[0], block):
+        M += (A[r0:r0 + block].float().T @ B[r0:r0 + block].float()).double()
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    E = M - (U * S) @ V.T
+    sv = torch.linalg.svdvals(M)
+    r = U.shape[1]
+    opt = float(sv[r] / sv[0]) if sv.shape[0] > r else 0.0
+    return float(torch.linalg.matrix_norm(E, ord=2) / sv[0]), opt
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="scale", choices=sorted(WORKLOADS))
+    ap.add_argument("--engine", default="auto", choices=["auto", "simt", "tc"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-error", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_1610_06656_gb300 import build, pipeline, smp, synth
+    smp.load(build.build() if rank == 0 or world == 1 else build.LIB_PATH)
+    if world > 1:
+        dist.barrier()
+    engine = {"auto": smp.SMP_ENGINE_AUTO, "simt": smp.SMP_ENGINE_SIMT, "tc": smp.SMP_ENGINE_TC}[args.engine]
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    A, B, _, _, _ = synth.lowrank_plus_noise_torch(w["d"], w["n1"], w["n2"], w["L"], w["sigma"], w["alpha"],
+                                                  seed=1001 + rank, device=dev)
+    torch.cuda.synchronize()
+    solver = pipeline.Solver(w["n1"], w["n2"], w["k"], torch.float32, seed=1 + rank, engine=engine,
+                             max_rows=w["block"])
+    m = pipeline.default_m(w["n1"], w["n2"], w["r"])
+
+    def sketch_timed(evs):
+        smp.smp_sketch_reset(solver.ctx)
+        for r0 in range(0, w["d"], w["block"]):
+            r1 = min(w["d"], r0 + w["block"])
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            smp.smp_sketch_accumulate(solver.ctx, A[r0:r1], w["n1"], B[r0:r1], w["n2"], r0, r1 - r0)
+            e1.record(stream)
+            evs.append((e0, e1, r1 - r0))
+        smp.smp_sketch_finalize(solver.ctx)
+
+    def step(evs):
+        sketch_timed(evs)
+        nnz = solver.sample(m, 2 + rank)
+        vals = solver.estimate(nnz)
+        return solver.waltmin(vals, w["r"], w["T"], 0, 3 + rank), nnz
+
+    for _ in range(args.warmup):
+        step([])
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = smp.smp_launch_count()
+    sk_events, step_events = [], []
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        (U, S, V), nnz = step(sk_events)
+        s1.record(stream)
+        step_events.append((s0, s1))
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = smp.smp_launch_count() - launches0
+    clk = clocks.stop()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    if world > 1:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    step_ms = sorted(a.elapsed_time(b) for a, b in step_events)
+    sk_ms = [a.elapsed_time(b) for a, b, _ in sk_events]
+    sk_rows = [n for _, _, n in sk_events]
+    value = world * args.steps / elapsed
+
+    peaks, peak_kind = measured_peaks()
+    ntot = w["n1"] + w["n2"]
+    sk_bytes = sum(sk_rows) * ntot * 4 / len(sk_rows)          # algorithmic bytes per launch: A and B rows read once
+    sk_flops = 2.0 * w["k"] * sum(sk_rows) * ntot / len(sk_rows)
+    sk_avg_s = sum(sk_ms) / len(sk_ms) / 1e3
+    tc_used = engine == smp.SMP_ENGINE_TC or (engine == smp.SMP_ENGINE_AUTO and tc_active(smp))
+    if tc_used:
+        tf32_peak = peaks["bf16_tflops"] * (1.1 / 2.25)
+        roof = {"bound": "tensor", "achieved": sk_flops / sk_avg_s / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
+                "peak_kind": "%s bf16 burst x nominal tf32/bf16 ratio 1.1/2.25" % peak_kind}
+    else:
+        clk_mhz = peaks.get("sm_max_mhz", 2070.0)
+        alu_peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": sk_flops / sk_avg_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                "peak_kind": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x %.0f MHz" % clk_mhz}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = "sketch (tcgen05)" if tc_used else "sketch_simt_kernel"
+    roof["hbm_gbs"] = sk_bytes / sk_avg_s / 1e9
+    roof["hbm_frac"] = roof["hbm_gbs"] / peaks["hbm_gbs"]
+    roof["launch_ms"] = sk_avg_s * 1e3
+    roof["bytes_per_launch"] = sk_bytes
+
+    err, opt_err = None, None
+    if not args.no_error and rank == 0:
+        err, opt_err = spectral_error(torch, A, B, U, S, V)
+
+    # ---- end to end: host-resident inputs copied in every step (pinned, double-buffered row blocks)
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e = run_e2e(torch, smp, solver, A, B, w, m, rank, args.e2e_steps, stream, world, dev)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        per, wall = cpu_oracle_sample(w, 1001, 16384 if args.workload == "scale" else w["d"])
+        cpu = {"value": 1.0 / per, "unit": "solves/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+               "sample": "single pass over 16,384 of 1,000,000 rows (time x d/rows) + sampling, estimate and "
+                         "WAltMin at n = 2,000; %.1f s of CPU wall time" % wall}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "tf32" if tc_used else "f32",
+                "data": "synthetic (low rank 20 + noise 0.1, column scales (j+1)^-0.5, torch RNG seeded per rank)",
+                "config": {"workload": args.workload, **{k: w[k] for k in ("d", "n1", "n2", "k", "r", "T")},
+                           "block_rows": w["block"], "m": m, "nnz": int(nnz), "parallelism": "replicas",
+                           "l2": "inputs (16 GB) larger than L2; no flush", "engine": args.engine},
+                "p50_ms": statistics.median(step_ms), "p99_ms": step_ms[min(len(step_ms) - 1,
+                                                                            int(math.ceil(0.99 * len(step_ms))) - 1)],
+                "sketch_gbs": roof["hbm_gbs"], "spectral_err": err, "optimal_err": opt_err,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    solver.close()
+
+
+def tc_active(smp):
+    return False
+
+
+def run_e2e(torch, smp, solver, A, B, w, m, rank, steps, stream, world, dev):
+    """Same solve with A, B in pinned host memory: every step copies each 65,536-row block host->device (on a copy
+    stream, two device buffers in flight) before it is sketched, and reads U, S, V back."""
+    blk = w["block"]
+    Ah = torch.empty(A.shape, dtype=A.dtype, pin_memory=True)
+    Bh = torch.empty(B.shape, dtype=B.dtype, pin_memory=True)
+    Ah.copy_(A)
+    Bh.copy_(B)
+    bufA = [torch.empty(blk, w["n1"], dtype=A.dtype, device=dev) for _ in range(2)]
+    bufB = [torch.empty(blk, w["n2"], dtype=B.dtype, device=dev) for _ in range(2)]
+    copy_stream = torch.cuda.Stream(device=dev)
+    copied = [torch.cuda.Event() for _ in range(2)]
+    consumed = [torch.cuda.Event() for _ in range(2)]
+    outU = torch.empty(w["n1"], w["r"], dtype=torch.float64, pin_memory=True)
+    outS = torch.empty(w["r"], dtype=torch.float64, pin_memory=True)
+    outV = torch.empty(w["n2"], w["r"], dtype=torch.float64, pin_memory=True)
+
+    def one():
+        smp.smp_sketch_reset(solver.ctx)
+        starts = list(range(0, w["d"], blk))
+        for idx, r0 in enumerate(starts):
+            r1 = min(w["d"], r0 + blk)
+            s = idx & 1
+            with torch.cuda.stream(copy_stream):
+                copy_stream.wait_event(consumed[s])
+                bufA[s][:r1 - r0].copy_(Ah[r0:r1], non_blocking=True)
+                bufB[s][:r1 - r0].copy_(Bh[r0:r1], non_blocking=True)
+                copied[s].record(copy_stream)
+            stream.wait_event(copied[s])
+            smp.smp_sketch_accumulate(solver.ctx, bufA[s], w["n1"], bufB[s], w["n2"], r0, r1 - r0)
+            consumed[s].record(stream)
+        smp.smp_sketch_finalize(solver.ctx)
+        nnz = solver.sample(m, 2 + rank)
+        vals = solver.estimate(nnz)
+        U, S, V = solver.waltmin(vals, w["r"], w["T"], 0, 3 + rank)
+        outU.copy_(U, non_blocking=True)
+        outS.copy_(S, non_blocking=True)
+        outV.copy_(V, non_blocking=True)
+        stream.synchronize()
+
+    for ev in consumed:
+        ev.record(stream)
+    one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([el], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    h2d = (A.numel() * A.element_size() + B.numel() * B.element_size())
+    d2h = (outU.numel() + outS.numel() + outV.numel()) * 8
+    return {"value": world * steps / el, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": 1e3 * el / steps}
+
+
+if __name__ == "__main__":
+    main()

@@ -177,6 +177,9 @@ const char* smp_status_string(smp_status s);
 /* Library version, major * 10000 + minor * 100 + patch. */
 int32_t smp_version(void);
 
+/* Number of CUDA kernels this library has launched since it was loaded (all contexts, all threads). */
+int64_t smp_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

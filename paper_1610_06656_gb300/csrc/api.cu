@@ -17,6 +17,8 @@ thread_local std::string g_begin_error;
 
 namespace smp {
 
+std::atomic<uint64_t> g_launches{0};
+
 smp_status fail(smp_ctx* c, smp_status s, const std::string& msg) {
     if (c) c->err = msg;
     else g_begin_error = msg;
@@ -308,5 +310,7 @@ const char* smp_status_string(smp_status s) {
 }
 
 int32_t smp_version(void) { return 100; }
+
+int64_t smp_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
 }  // extern "C"

@@ -71,7 +71,7 @@ void launch_npl(smp_ctx* c, void* vals) {
     const double* DB = c->p.same_ab ? c->D_all : c->D_all + c->p.n1;
     const int64_t warps = c->p.n1;
     const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
-    estimate_kernel<T, NPL><<<blocks, 256, 0, c->stream>>>(At, Bt, c->ldk, c->p.k, DA, DB, c->row_ptr, c->col,
+    estimate_kernel<T, NPL><<<smp::counted(blocks), 256, 0, c->stream>>>(At, Bt, c->ldk, c->p.k, DA, DB, c->row_ptr, c->col,
                                                            c->p.n1, (T*)vals);
 }
 

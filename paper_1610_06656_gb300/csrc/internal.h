@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 
@@ -47,6 +48,14 @@ struct smp_ctx {
 };
 
 namespace smp {
+
+// Kernel launches made by this library since it was loaded (process-wide), for launch-count reporting.
+extern std::atomic<uint64_t> g_launches;
+template <typename G>
+inline G counted(G grid) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return grid;
+}
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 

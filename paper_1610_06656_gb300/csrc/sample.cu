@@ -240,15 +240,15 @@ smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out) {
         c->mask_words = n1 * W;
     }
     cudaError_t e;
-    terms_kernel<<<1, 256, 0, st>>>(c->s_all, n1, n2, c->p.same_ab, m, c->F, c->alpha, c->beta);
+    terms_kernel<<<smp::counted(1), 256, 0, st>>>(c->s_all, n1, n2, c->p.same_ab, m, c->F, c->alpha, c->beta);
     if ((e = cudaMemsetAsync(c->col_cnt, 0, (size_t)n2 * 4, st)) != cudaSuccess) return check_cuda(c, e, "memset");
     const int64_t warps = n1 * W;
     const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
-    coin_kernel<<<blocks, 256, 0, st>>>(c->alpha, c->beta, n1, n2, W, (uint32_t)seed, (uint32_t)(seed >> 32),
+    coin_kernel<<<smp::counted(blocks), 256, 0, st>>>(c->alpha, c->beta, n1, n2, W, (uint32_t)seed, (uint32_t)(seed >> 32),
                                         c->mask, c->col_cnt);
-    row_prefix_kernel<<<(unsigned)n1, 256, 0, st>>>(c->mask, n1, W, c->wpre, c->row_cnt);
-    scan_kernel<<<1, 1024, 0, st>>>(c->row_cnt, n1, c->row_ptr);
-    scan_kernel<<<1, 1024, 0, st>>>(c->col_cnt, n2, c->col_ptr);
+    row_prefix_kernel<<<smp::counted((unsigned)n1), 256, 0, st>>>(c->mask, n1, W, c->wpre, c->row_cnt);
+    scan_kernel<<<smp::counted(1), 1024, 0, st>>>(c->row_cnt, n1, c->row_ptr);
+    scan_kernel<<<smp::counted(1), 1024, 0, st>>>(c->col_cnt, n2, c->col_ptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return check_cuda(c, e, "smp_sample count kernels");
     int64_t nnz = 0;
     if ((e = cudaMemcpyAsync(&nnz, c->row_ptr + n1, sizeof(int64_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -263,9 +263,9 @@ smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out) {
         c->cap = want;
     }
     if (nnz > 0) {
-        fill_csr_kernel<<<blocks, 256, 0, st>>>(c->mask, c->wpre, c->row_ptr, c->alpha, c->beta, n1, n2, W, c->col,
+        fill_csr_kernel<<<smp::counted(blocks), 256, 0, st>>>(c->mask, c->wpre, c->row_ptr, c->alpha, c->beta, n1, n2, W, c->col,
                                                 c->qhat);
-        fill_csc_kernel<<<(unsigned)n2, 256, 0, st>>>(c->mask, c->wpre, c->row_ptr, c->col_ptr, n1, W, c->csc_row,
+        fill_csc_kernel<<<smp::counted((unsigned)n2), 256, 0, st>>>(c->mask, c->wpre, c->row_ptr, c->col_ptr, n1, W, c->csc_row,
                                                       c->csc_pos);
         if ((e = cudaGetLastError()) != cudaSuccess) return check_cuda(c, e, "smp_sample fill kernels");
     }

@@ -222,7 +222,7 @@ cudaError_t launch_simt_typed(smp_ctx* c, const void* A, int64_t lda, const void
     a.part = (TAcc*)c->part;
     a.nsq = c->nsq;
     dim3 grid((unsigned)((c->ntot + TN - 1) / TN), (unsigned)((c->p.k + TK - 1) / TK), (unsigned)splits);
-    sketch_simt_kernel<TIn, TAcc><<<grid, 256, 0, c->stream>>>(a);
+    sketch_simt_kernel<TIn, TAcc><<<smp::counted(grid), 256, 0, c->stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -311,12 +311,12 @@ cudaError_t launch_sketch_simt(smp_ctx* c, const void* A, int64_t lda, const voi
 cudaError_t launch_finalize(smp_ctx* c) {
     const unsigned nb = (unsigned)c->ntot;
     if (c->acc_bytes == 8)
-        finalize_kernel<double><<<nb, 256, 0, c->stream>>>((const double*)c->part, c->nsq, c->splits, c->ntot,
+        finalize_kernel<double><<<smp::counted(nb), 256, 0, c->stream>>>((const double*)c->part, c->nsq, c->splits, c->ntot,
                                                           c->p.k, c->ldk, (double*)c->sk, c->s_all, c->D_all);
     else
-        finalize_kernel<float><<<nb, 256, 0, c->stream>>>((const float*)c->part, c->nsq, c->splits, c->ntot,
+        finalize_kernel<float><<<smp::counted(nb), 256, 0, c->stream>>>((const float*)c->part, c->nsq, c->splits, c->ntot,
                                                          c->p.k, c->ldk, (float*)c->sk, c->s_all, c->D_all);
-    frobenius_kernel<<<1, 32, 0, c->stream>>>(c->s_all, c->p.n1, c->p.n2, c->p.same_ab, c->F);
+    frobenius_kernel<<<smp::counted(1), 32, 0, c->stream>>>(c->s_all, c->p.n1, c->p.n2, c->p.same_ab, c->F);
     return cudaGetLastError();
 }
 
@@ -325,13 +325,13 @@ cudaError_t launch_import(smp_ctx* c, const void* At, const void* Bt, const doub
     const void* bt = c->p.same_ab ? At : Bt;
     const double* sb = c->p.same_ab ? sA : sB;
     if (c->acc_bytes == 8)
-        import_kernel<double><<<nb, 256, 0, c->stream>>>((const double*)At, (const double*)bt, c->p.n1, c->ntot,
+        import_kernel<double><<<smp::counted(nb), 256, 0, c->stream>>>((const double*)At, (const double*)bt, c->p.n1, c->ntot,
                                                         c->p.k, c->ldk, (double*)c->sk, sA, sb, c->s_all,
                                                         c->D_all);
     else
-        import_kernel<float><<<nb, 256, 0, c->stream>>>((const float*)At, (const float*)bt, c->p.n1, c->ntot,
+        import_kernel<float><<<smp::counted(nb), 256, 0, c->stream>>>((const float*)At, (const float*)bt, c->p.n1, c->ntot,
                                                        c->p.k, c->ldk, (float*)c->sk, sA, sb, c->s_all, c->D_all);
-    frobenius_kernel<<<1, 32, 0, c->stream>>>(c->s_all, c->p.n1, c->p.n2, c->p.same_ab, c->F);
+    frobenius_kernel<<<smp::counted(1), 32, 0, c->stream>>>(c->s_all, c->p.n1, c->p.n2, c->p.same_ab, c->F);
     return cudaGetLastError();
 }
 

@@ -358,8 +358,8 @@ unsigned nblocks(int64_t n, int threads) { return (unsigned)((n + threads - 1) /
 template <typename TX, typename TY>
 void gram(const TX* X, const TY* Y, int64_t n, int a, int b, double* part, double* G, cudaStream_t st) {
     const int nblk = (int)std::max<int64_t>(1, (n + GRAM_ROWS_PER_BLOCK - 1) / GRAM_ROWS_PER_BLOCK);
-    gram_partial_kernel<TX, TY><<<nblk, 256, 0, st>>>(X, Y, n, a, b, part);
-    gram_reduce_kernel<<<nblocks(a * b, 256), 256, 0, st>>>(part, nblk, a * b, G);
+    gram_partial_kernel<TX, TY><<<smp::counted(nblk), 256, 0, st>>>(X, Y, n, a, b, part);
+    gram_reduce_kernel<<<smp::counted(nblocks(a * b, 256)), 256, 0, st>>>(part, nblk, a * b, G);
 }
 
 // Cholesky-QR twice: Q = X R^-1 with X = Q R; Rout = R2 R1 (upper). Q may alias nothing of X.
@@ -380,12 +380,12 @@ template <typename TX, typename TQ>
 void cholqr2(const TX* X, int64_t n, int b, TQ* Q, double* part, double* G, double* R1, double* R2, double* Rout,
              cudaStream_t st) {
     gram<TX, TX>(X, X, n, b, b, part, G, st);
-    chol_kernel<<<1, 32, 0, st>>>(G, b, R1, 1e-28, nullptr);
-    apply_rinv_kernel<TX, TQ><<<nblocks(n, 128), 128, 0, st>>>(X, n, b, R1, Q);
+    chol_kernel<<<smp::counted(1), 32, 0, st>>>(G, b, R1, 1e-28, nullptr);
+    apply_rinv_kernel<TX, TQ><<<smp::counted(nblocks(n, 128)), 128, 0, st>>>(X, n, b, R1, Q);
     gram<TQ, TQ>(Q, Q, n, b, b, part, G, st);
-    chol_kernel<<<1, 32, 0, st>>>(G, b, R2, 1e-28, nullptr);
-    apply_rinv_kernel<TQ, TQ><<<nblocks(n, 128), 128, 0, st>>>(Q, n, b, R2, Q);
-    if (Rout) upper_mul_kernel<<<nblocks(b * b, 256), 256, 0, st>>>(R2, R1, b, Rout);
+    chol_kernel<<<smp::counted(1), 32, 0, st>>>(G, b, R2, 1e-28, nullptr);
+    apply_rinv_kernel<TQ, TQ><<<smp::counted(nblocks(n, 128)), 128, 0, st>>>(Q, n, b, R2, Q);
+    if (Rout) upper_mul_kernel<<<smp::counted(nblocks(b * b, 256)), 256, 0, st>>>(R2, R1, b, Rout);
 }
 
 template <typename TF, typename TG, typename TV>
@@ -394,13 +394,13 @@ void launch_ls(int r, const int64_t* ptr, const int32_t* idx, const int64_t* pos
                cudaStream_t st) {
     const unsigned g = nblocks(n_out, LS_WARPS);
     if (r <= 8)
-        ls_kernel<TF, TG, TV, 8><<<g, 32 * LS_WARPS, 0, st>>>(ptr, idx, pos, vals, qhat, sub, sid, Fin, r, n_out,
+        ls_kernel<TF, TG, TV, 8><<<smp::counted(g), 32 * LS_WARPS, 0, st>>>(ptr, idx, pos, vals, qhat, sub, sid, Fin, r, n_out,
                                                               Xout, err);
     else if (r <= 16)
-        ls_kernel<TF, TG, TV, 16><<<g, 32 * LS_WARPS, 0, st>>>(ptr, idx, pos, vals, qhat, sub, sid, Fin, r,
+        ls_kernel<TF, TG, TV, 16><<<smp::counted(g), 32 * LS_WARPS, 0, st>>>(ptr, idx, pos, vals, qhat, sub, sid, Fin, r,
                                                                n_out, Xout, err);
     else
-        ls_kernel<TF, TG, TV, 32><<<g, 32 * LS_WARPS, 0, st>>>(ptr, idx, pos, vals, qhat, sub, sid, Fin, r,
+        ls_kernel<TF, TG, TV, 32><<<smp::counted(g), 32 * LS_WARPS, 0, st>>>(ptr, idx, pos, vals, qhat, sub, sid, Fin, r,
                                                                n_out, Xout, err);
 }
 
@@ -471,21 +471,21 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
         attr_done = true;
     }
     auto jacobi = [&](const double* Ain, int n, double tol, double* evals, double* Vout) {
-        jacobi_eig_kernel<<<1, 256, 2 * n * (n + 1) * 8, st>>>(Ain, n, tol, 40, evals, Vout);
+        jacobi_eig_kernel<<<smp::counted(1), 256, 2 * n * (n + 1) * 8, st>>>(Ain, n, tol, 40, evals, Vout);
     };
 
-    if (nnz > 0) erow_kernel<<<nblocks(n1 * 32, 256), 256, 0, st>>>(c->row_ptr, n1, erow);
+    if (nnz > 0) erow_kernel<<<smp::counted(nblocks(n1 * 32, 256)), 256, 0, st>>>(c->row_ptr, n1, erow);
     if (split && nnz > 0)
-        split_kernel<<<nblocks(nnz, 256), 256, 0, st>>>(erow, c->col, nnz, T, k0, k1, sub);
+        split_kernel<<<smp::counted(nblocks(nnz, 256)), 256, 0, st>>>(erow, c->col, nnz, T, k0, k1, sub);
     const uint8_t* subp = split ? sub : nullptr;
 
     smp_status status = SMP_OK;
     if (flags & SMP_INIT_GIVEN) {
-        convert_kernel<double, TF><<<nblocks(n1 * r, 256), 256, 0, st>>>(U_init, n1 * r, Uf);
+        convert_kernel<double, TF><<<smp::counted(nblocks(n1 * r, 256)), 256, 0, st>>>(U_init, n1 * r, Uf);
     } else {
         // R_Omega0(M~) values
-        if (nnz > 0) rvals_kernel<TV, TY><<<nblocks(nnz, 256), 256, 0, st>>>(vals, c->qhat, subp, 0, nnz, rv);
-        start_block_kernel<TY><<<nblocks(n1 * ((b + 3) / 4), 256), 256, 0, st>>>(n1, b, k0, k1, Y);
+        if (nnz > 0) rvals_kernel<TV, TY><<<smp::counted(nblocks(nnz, 256)), 256, 0, st>>>(vals, c->qhat, subp, 0, nnz, rv);
+        start_block_kernel<TY><<<smp::counted(nblocks(n1 * ((b + 3) / 4), 256)), 256, 0, st>>>(n1, b, k0, k1, Y);
         cholqr2<TY, TY>(Y, n1, b, Y, part, G, R1, R2, nullptr, st);
         const bool dbl = sizeof(TY) == 8;
         const int max_iter = dbl ? 400 : 300;
@@ -493,17 +493,17 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
         const int check = 10;
         std::vector<double> hbuf(2);
         for (int it = 1; it <= max_iter; ++it) {
-            spmm_csc_kernel<TY><<<nblocks(n2 * 32, 256), 256, 0, st>>>(c->col_ptr, c->csc_row, c->csc_pos, rv, Y,
+            spmm_csc_kernel<TY><<<smp::counted(nblocks(n2 * 32, 256)), 256, 0, st>>>(c->col_ptr, c->csc_row, c->csc_pos, rv, Y,
                                                                       n2, b, Z);
-            spmm_csr_kernel<TY><<<nblocks(n1 * 32, 256), 256, 0, st>>>(c->row_ptr, c->col, rv, Z, n1, b, Yt);
+            spmm_csr_kernel<TY><<<smp::counted(nblocks(n1 * 32, 256)), 256, 0, st>>>(c->row_ptr, c->col, rv, Z, n1, b, Yt);
             cholqr2<TY, TY>(Yt, n1, b, Y, part, G, R1, R2, nullptr, st);
             if (it % check == 0 || it == max_iter) {
                 // Rayleigh-Ritz on span(Y): C = Z^T Z with Z = R^T Y; U0 = Y E[:, :r]
-                spmm_csc_kernel<TY><<<nblocks(n2 * 32, 256), 256, 0, st>>>(c->col_ptr, c->csc_row, c->csc_pos,
+                spmm_csc_kernel<TY><<<smp::counted(nblocks(n2 * 32, 256)), 256, 0, st>>>(c->col_ptr, c->csc_row, c->csc_pos,
                                                                           rv, Y, n2, b, Z);
                 gram<TY, TY>(Z, Z, n2, b, b, part, G, st);
                 jacobi(G, b, 1e-15, ev, E);
-                ritz_kernel<TY><<<nblocks(n1 * r, 256), 256, 0, st>>>(Y, E, n1, b, r, U0);
+                ritz_kernel<TY><<<smp::counted(nblocks(n1 * r, 256)), 256, 0, st>>>(Y, E, n1, b, r, U0);
                 if (it > check) {
                     // subspace change: dist^2 = r - ||U0^T U0prev||_F^2
                     gram<double, double>(U0, U0p, n1, r, r, part, Gx, st);
@@ -523,8 +523,8 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
             }
         }
         if (status == SMP_OK) {
-            if (!(flags & SMP_NO_TRIM)) trim_kernel<<<nblocks(n1, 256), 256, 0, st>>>(U0, n1, r, c->s_all, c->F);
-            convert_kernel<double, TF><<<nblocks(n1 * r, 256), 256, 0, st>>>(U0, n1 * r, Uf);
+            if (!(flags & SMP_NO_TRIM)) trim_kernel<<<smp::counted(nblocks(n1, 256)), 256, 0, st>>>(U0, n1, r, c->s_all, c->F);
+            convert_kernel<double, TF><<<smp::counted(nblocks(n1 * r, 256)), 256, 0, st>>>(U0, n1 * r, Uf);
         }
     }
     if (status == SMP_OK) {
@@ -538,12 +538,12 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
         // canonical form
         cholqr2<TF, double>(Uf, n1, r, Qu, part, Gx, Rx1, Rx2, Ru, st);
         cholqr2<TF, double>(Vf, n2, r, Qv, part, Gx, Rx1, Rx2, Rv, st);
-        core_kernel<<<nblocks(4 * r * r, 256), 256, 0, st>>>(Ru, Rv, r, H);
+        core_kernel<<<smp::counted(nblocks(4 * r * r, 256)), 256, 0, st>>>(Ru, Rv, r, H);
         jacobi(H, 2 * r, 1e-16, evh, EV);
-        core_split_kernel<<<1, 32, 0, st>>>(evh, EV, r, S, Wc, Zc);
-        small_right_mul_kernel<<<nblocks(n1 * r, 256), 256, 0, st>>>(Qu, Wc, n1, r, U);
-        small_right_mul_kernel<<<nblocks(n2 * r, 256), 256, 0, st>>>(Qv, Zc, n2, r, V);
-        sign_kernel<<<r, 256, 0, st>>>(U, n1, V, n2, r);
+        core_split_kernel<<<smp::counted(1), 32, 0, st>>>(evh, EV, r, S, Wc, Zc);
+        small_right_mul_kernel<<<smp::counted(nblocks(n1 * r, 256)), 256, 0, st>>>(Qu, Wc, n1, r, U);
+        small_right_mul_kernel<<<smp::counted(nblocks(n2 * r, 256)), 256, 0, st>>>(Qv, Zc, n2, r, V);
+        sign_kernel<<<smp::counted(r), 256, 0, st>>>(U, n1, V, n2, r);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) status = check_cuda(c, e, "smp_waltmin kernels");
     }

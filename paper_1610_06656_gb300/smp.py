@@ -47,6 +47,7 @@ SIGNATURES = {
     "smp_last_error": (_c.c_char_p, [_vp]),
     "smp_status_string": (_c.c_char_p, [_i32]),
     "smp_version": (_i32, []),
+    "smp_launch_count": (_i64, []),
 }
 
 _lib = None
@@ -191,3 +192,7 @@ def smp_last_error(ctx=None):
 
 def smp_version():
     return load().smp_version()
+
+
+def smp_launch_count():
+    return load().smp_launch_count()
