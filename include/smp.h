@@ -177,6 +177,27 @@ const char* smp_status_string(smp_status s);
 /* Library version, major * 10000 + minor * 100 + patch. */
 int32_t smp_version(void);
 
+/* Allocation-free sketch of one row range. The paper has no counterpart: this call exists for callers that hold
+ * device buffers but may not allocate device memory themselves, e.g. a plug-in inside a host framework that owns
+ * the whole device-memory budget through its own pool, or a latency-critical loop where cudaMalloc / cudaFree would
+ * synchronise the device and stall other streams.
+ * It computes what smp_sketch_begin + one smp_sketch_accumulate(row0, nrows) + smp_sketch_finalize would (same
+ * Philox Pi, same SIMT kernel) and writes it to the caller's device buffers: At_dev (n1 x k row-major, row i =
+ * sketch column At_i), Bt_dev (n2 x k), sA_dev (n1 doubles, ||A_i||^2 over the range) and sB_dev (n2 doubles).
+ * A_dev / B_dev: nrows x n1 / nrows x n2 row-major, lda >= n1, ldb >= n2, dtype SMP_F32 or SMP_BF16 (others:
+ * SMP_EUNSUPPORTED). Asynchronous on stream (a cudaStream_t).
+ * Scratch: a fixed array of SMP_NOALLOC_SCRATCH_BYTES (16 MiB) compiled into the library, held on every GPU that
+ * loads it until the process exits. The partials need (n1 + n2) * (round_up(k, 4) * 4 + 8) bytes (each part rounded
+ * up to 256 bytes); larger shapes are rejected with SMP_EINVAL before anything is launched. The call performs no
+ * cudaMalloc / cudaFree. The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current and caches it: make that first call before any stream capture. Every call on a device
+ * shares the one array and clears the part it uses, so calls whose work overlaps on the GPU (other streams, other
+ * host threads) race and must be serialised by the caller. */
+#define SMP_NOALLOC_SCRATCH_BYTES (16u << 20)
+smp_status smp_sketch_noalloc(const void* A_dev, int64_t lda, const void* B_dev, int64_t ldb, int64_t n1,
+                              int64_t n2, int32_t k, int32_t dtype, uint64_t seed, int64_t row0, int64_t nrows,
+                              float* At_dev, float* Bt_dev, double* sA_dev, double* sB_dev, void* stream);
+
 /* Number of CUDA kernels this library has launched since it was loaded (all contexts, all threads). */
 int64_t smp_launch_count(void);
 

@@ -64,6 +64,10 @@ cudaError_t launch_sketch_simt(smp_ctx* c, const void* A, int64_t lda, const voi
                                int64_t nrows, const void* Pi, int64_t ldp);
 cudaError_t launch_finalize(smp_ctx* c);
 cudaError_t launch_import(smp_ctx* c, const void* At, const void* Bt, const double* sA, const double* sB);
+cudaError_t launch_sketch_simt_into(int dtype, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1,
+                                    int64_t n2, int k, uint64_t seed, int64_t row0, int64_t nrows, float* part,
+                                    double* nsq, int splits, int sm_count, float* At, float* Bt, double* sA,
+                                    double* sB, cudaStream_t st);
 
 // sketch_tc.cu
 bool tc_supported(const smp_ctx* c);

@@ -335,4 +335,78 @@ cudaError_t launch_import(smp_ctx* c, const void* At, const void* Bt, const doub
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------------------------------
+// The same SIMT sketch over one row range with caller-supplied split partials, and the fixed-order reduction of
+// those partials into dense caller outputs. Used only by the allocation-free entry point in noalloc.cu.
+// ---------------------------------------------------------------------------------------------------------------
+namespace {
+
+__global__ void __launch_bounds__(256) reduce_into_kernel(const float* __restrict__ part,
+                                                          const double* __restrict__ nsq, int splits, int64_t n1,
+                                                          int64_t ntot, int k, int64_t ldk, float* At, float* Bt,
+                                                          double* sA, double* sB) {
+    const int64_t c = blockIdx.x;
+    float* dst = c < n1 ? At + c * k : Bt + (c - n1) * k;
+    for (int a = threadIdx.x; a < k; a += blockDim.x) {
+        float v = 0.0f;
+        for (int s = 0; s < splits; ++s) v += part[((int64_t)s * ntot + c) * ldk + a];
+        dst[a] = v;
+    }
+    if (threadIdx.x == 0) {
+        double sc = 0.0;
+        for (int s = 0; s < splits; ++s) sc += nsq[(int64_t)s * ntot + c];
+        if (c < n1) sA[c] = sc;
+        else sB[c - n1] = sc;
+    }
+}
+
+template <typename TIn>
+cudaError_t sketch_into_typed(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1, int64_t n2, int k,
+                              uint64_t seed, int64_t row0, int64_t nrows, float* part, double* nsq, int splits,
+                              int sm_count, cudaStream_t st) {
+    SketchArgs<TIn, float> a;
+    a.A = (const TIn*)A;
+    a.B = (const TIn*)B;
+    a.Pi = nullptr;
+    a.lda = lda;
+    a.ldb = ldb;
+    a.ldp = 0;
+    a.n1 = n1;
+    a.ntot = n1 + n2;
+    a.row0 = row0;
+    a.nrows = nrows;
+    const int64_t steps = (nrows + TR - 1) / TR;
+    const int64_t tiles = ((a.ntot + TN - 1) / TN) * ((k + TK - 1) / TK);
+    int used = (int)std::min<int64_t>(splits, std::max<int64_t>(1, (2 * sm_count + tiles - 1) / tiles));
+    used = (int)std::min<int64_t>(used, std::max<int64_t>(1, steps));
+    a.rows_per_split = ((steps + used - 1) / used) * TR;
+    a.k = k;
+    a.ldk = round_up(k, 4);
+    a.key0 = (uint32_t)seed;
+    a.key1 = (uint32_t)(seed >> 32);
+    a.scale = (float)(1.0 / sqrt((double)k));
+    a.part = part;
+    a.nsq = nsq;
+    dim3 grid((unsigned)((a.ntot + TN - 1) / TN), (unsigned)((k + TK - 1) / TK), (unsigned)used);
+    if (nrows > 0) sketch_simt_kernel<TIn, float><<<smp::counted(grid), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_sketch_simt_into(int dtype, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1,
+                                    int64_t n2, int k, uint64_t seed, int64_t row0, int64_t nrows, float* part,
+                                    double* nsq, int splits, int sm_count, float* At, float* Bt, double* sA,
+                                    double* sB, cudaStream_t st) {
+    cudaError_t e = dtype == SMP_BF16
+                        ? sketch_into_typed<__nv_bfloat16>(A, lda, B, ldb, n1, n2, k, seed, row0, nrows, part, nsq,
+                                                           splits, sm_count, st)
+                        : sketch_into_typed<float>(A, lda, B, ldb, n1, n2, k, seed, row0, nrows, part, nsq, splits,
+                                                   sm_count, st);
+    if (e != cudaSuccess) return e;
+    reduce_into_kernel<<<smp::counted((unsigned)(n1 + n2)), 256, 0, st>>>(part, nsq, splits, n1, n1 + n2, k,
+                                                                          round_up(k, 4), At, Bt, sA, sB);
+    return cudaGetLastError();
+}
+
 }  // namespace smp

@@ -48,6 +48,8 @@ SIGNATURES = {
     "smp_status_string": (_c.c_char_p, [_i32]),
     "smp_version": (_i32, []),
     "smp_launch_count": (_i64, []),
+    "smp_sketch_noalloc": (_i32, [_vp, _i64, _vp, _i64, _i64, _i64, _i32, _i32, _u64, _i64, _i64, _vp, _vp, _vp,
+                                  _vp, _vp]),
 }
 
 _lib = None
@@ -192,6 +194,13 @@ def smp_last_error(ctx=None):
 
 def smp_version():
     return load().smp_version()
+
+
+def smp_sketch_noalloc(A, lda, B, ldb, n1, n2, k, dtype, seed, row0, nrows, At, Bt, sA, sB, stream=None):
+    """Allocation-free sketch of one row range into caller buffers (see include/smp.h)."""
+    _check(load().smp_sketch_noalloc(_ptr(A), lda, _ptr(B), ldb, n1, n2, k, dtype, seed & 0xFFFFFFFFFFFFFFFF, row0,
+                                     nrows, _ptr(At), _ptr(Bt), _ptr(sA), _ptr(sB), _stream(stream)),
+           "smp_sketch_noalloc")
 
 
 def smp_launch_count():
