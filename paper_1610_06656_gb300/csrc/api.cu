@@ -39,7 +39,9 @@ smp_status read_device_error(smp_ctx* c) {
     if (e != cudaSuccess) return check_cuda(c, e, "reading the device error word");
     if (h == 0) return SMP_OK;
     cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream);
-    if (h & DEVERR_TIMEOUT) return fail(c, SMP_ETIMEOUT, "a bounded device-side wait gave up");
+    char word[32];
+    snprintf(word, sizeof(word), " (error word 0x%x)", h);
+    if (h & DEVERR_TIMEOUT) return fail(c, SMP_ETIMEOUT, std::string("a bounded device-side wait gave up") + word);
     if (h & DEVERR_NUMERIC) return fail(c, SMP_ENUMERIC, "a Cholesky pivot was not positive");
     return fail(c, SMP_ECUDA, "a kernel index check failed");
 }
@@ -153,9 +155,11 @@ smp_status smp_sketch_accumulate(smp_ctx* c, const void* A, int64_t lda, const v
     smp_status s = check_block(c, A, lda, B, ldb, nrows);
     if (s != SMP_OK || nrows == 0) return s;
     if (row0 < 0) return fail(c, SMP_EINVAL, "row0 < 0");
-    const bool want_tc = c->p.engine == SMP_ENGINE_TC || (c->p.engine == SMP_ENGINE_AUTO && tc_supported(c));
-    if (c->p.engine == SMP_ENGINE_TC && !tc_supported(c))
-        return fail(c, SMP_EUNSUPPORTED, "the tensor-core sketch does not support this dtype / shape");
+    const bool tc_ok = tc_block_ok(c, A, lda, B, ldb);
+    if (c->p.engine == SMP_ENGINE_TC && !tc_ok)
+        return fail(c, SMP_EUNSUPPORTED,
+                    "the tensor-core sketch needs SMP_F32, k <= 512, 16-byte aligned blocks and lda, ldb % 4 == 0");
+    const bool want_tc = c->p.engine == SMP_ENGINE_TC || (c->p.engine == SMP_ENGINE_AUTO && tc_ok);
     cudaError_t e = want_tc ? launch_sketch_tc(c, A, lda, B, ldb, row0, nrows)
                             : launch_sketch_simt(c, A, lda, B, ldb, row0, nrows, nullptr, 0);
     return check_cuda(c, e, "smp_sketch_accumulate");
@@ -166,6 +170,12 @@ smp_status smp_sketch_accumulate_pi(smp_ctx* c, const void* Pi, int64_t ldp, con
     smp_status s = check_block(c, A, lda, B, ldb, nrows);
     if (s != SMP_OK || nrows == 0) return s;
     if (!Pi || ldp < nrows) return fail(c, SMP_EINVAL, "Pi_blk is null or ldp < nrows");
+    const bool tc_ok = tc_block_ok(c, A, lda, B, ldb) && ((uintptr_t)Pi % 16 == 0) && (ldp % 4 == 0);
+    if (c->p.engine == SMP_ENGINE_TC && !tc_ok)
+        return fail(c, SMP_EUNSUPPORTED, "the tensor-core sketch needs 16-byte aligned Pi and ldp % 4 == 0");
+    if (c->p.engine == SMP_ENGINE_TC || (c->p.engine == SMP_ENGINE_AUTO && tc_ok))
+        return check_cuda(c, launch_sketch_tc_pi(c, A, lda, B, ldb, row0, nrows, (const float*)Pi, ldp),
+                          "smp_sketch_accumulate_pi");
     return check_cuda(c, launch_sketch_simt(c, A, lda, B, ldb, row0, nrows, Pi, ldp), "smp_sketch_accumulate_pi");
 }
 

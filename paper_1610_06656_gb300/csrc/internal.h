@@ -71,8 +71,11 @@ cudaError_t launch_sketch_simt_into(int dtype, const void* A, int64_t lda, const
 
 // sketch_tc.cu
 bool tc_supported(const smp_ctx* c);
+bool tc_block_ok(const smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb);
 cudaError_t launch_sketch_tc(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t row0,
                              int64_t nrows);
+cudaError_t launch_sketch_tc_pi(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t row0,
+                                int64_t nrows, const float* Pi, int64_t ldp);
 
 // sample.cu
 smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out);

@@ -1,13 +1,530 @@
-// Tensor-core (tcgen05) sketch engine: placeholder until the sm_103a kernel lands; AUTO falls back to nothing
-// here because tc_supported() reports false, so the SIMT engine runs.
+// Tensor-core sketch engine for sm_103a (Algorithm 1, step 2; Section 2.1 "Step 1"): At += Pi[:, rows] A_blk and
+// Bt += Pi[:, rows] B_blk with TF32 operands and FP32 accumulation in TMEM, fused with the compensated column sums
+// of squares, so each element of A and B is read from HBM once.
+//
+// Two kernels per row block:
+//  1. pi_gen_kernel writes Pi[a][t] (t contiguous, rounded to TF32) for the block's rows into a context buffer.
+//     Generating Pi once per block and letting every column tile read it (through L2) costs one Gaussian per
+//     (sketch row, data row); regenerating it inside each column tile would cost (n1 + n2) / 128 times more.
+//  2. sketch_tc_kernel: one CTA per (128-column tile, row split). Warp 0 issues TMA loads of the data tile (rows
+//     of A are contiguous along the columns, so the tile lands column-major for the MMA: 32-column x 8-row
+//     boxes, 128-byte swizzle) and of the Pi tile (K-major, 64-byte swizzle, 256-row boxes) into a 4-stage
+//     shared-memory ring guarded by mbarriers. kind::tf32 takes K-major operands only, so warps 4-7 (one
+//     32-column box each) read every staged element once, fold x^2 into compensated (TwoSum + FMA residual)
+//     column sums, round x to TF32 (cvt.rna) and write it back K-major (64-byte swizzle, conflict-free 16-byte
+//     stores). Warp 1 (one thread) issues tcgen05.mma kind::tf32 with M = 128 data columns and N = 256 sketch
+//     rows per instruction into a TMEM accumulator of 128 lanes x up to 512 columns. Warps 4-7 then drain TMEM
+//     with tcgen05.ld and add the tile into the split's partial sketch. Every wait is bounded (%globaltimer); a
+//     timeout sets the device error word and the CTA unwinds.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "common.cuh"
 #include "internal.h"
 
 namespace smp {
+namespace {
 
-bool tc_supported(const smp_ctx*) { return false; }
+constexpr int TILE_M = 128;        // data columns per CTA (MMA M)
+constexpr int KS = 16;             // data rows per pipeline stage (two K = 8 MMA slices)
+constexpr int STAGES = 4;
+constexpr int PI_BOX_ROWS = 256;   // sketch rows per Pi box (MMA N)
+constexpr int MAX_KC = 512;        // sketch rows per CTA (TMEM columns)
+constexpr int DATA_BOX_ROWS = 8;
+constexpr int DATA_BOX_BYTES = 32 * DATA_BOX_ROWS * 4;      // 32 columns x 8 rows, fp32 (one swizzle atom)
+constexpr int DATA_STAGE_BYTES = 4 * KS * 32 * 4;           // 128 columns x KS rows: [8-row group][32-col box]
+constexpr int KGROUP_BYTES = 4 * DATA_BOX_BYTES;            // one 8-row group of all four boxes
+constexpr int A_STAGE_BYTES = TILE_M * KS * 4;             // K-major copy: 128 rows x 64 B (64-byte swizzle)
+constexpr int PI_BOX_BYTES = PI_BOX_ROWS * KS * 4;          // 256 rows x KS fp32
+constexpr int PI_STAGE_BYTES = 2 * PI_BOX_BYTES;
+constexpr int A_OFF = DATA_STAGE_BYTES;                     // offsets inside a stage
+constexpr int PI_OFF = DATA_STAGE_BYTES + A_STAGE_BYTES;
+constexpr int STAGE_BYTES = DATA_STAGE_BYTES + A_STAGE_BYTES + PI_STAGE_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+constexpr int THREADS = 256;
+constexpr unsigned long long WAIT_NS = 2000000000ull;       // 2 s: far beyond any legitimate wait
 
-cudaError_t launch_sketch_tc(smp_ctx*, const void*, int64_t, const void*, int64_t, int64_t, int64_t) {
-    return cudaErrorNotSupported;
+// ------------------------------------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long global_timer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false after WAIT_NS (the caller records the timeout and unwinds).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = global_timer();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_test(bar, parity)) return true;
+        if ((i & 255u) == 0) {
+            if (*abort_flag) return false;
+            if (global_timer() - t0 > WAIT_NS) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// 32 consecutive TMEM columns of this warp's 32 lanes (lane i of the warp <- TMEM lane base + i).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor (tcgen05): start >> 4 in bits 0-13, leading-dimension byte offset >> 4 in 16-29,
+// stride-dimension byte offset >> 4 in 32-45, descriptor version 1 in bits 46-47, swizzle mode in bits 61-63.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t swizzle) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)swizzle << 61;
+    return d;
+}
+constexpr uint32_t SWZ_128B = 2, SWZ_64B = 4;
+
+// Instruction descriptor, kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32 (bits 7-9, 10-12 = 2), both K-major
+// (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <typename T>
+__device__ __forceinline__ void two_sum_square(float x, float& hi, float& lo) {
+    const float p = __fmul_rn(x, x);
+    const float e = __fmaf_rn(x, x, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bp = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+// ------------------------------------------------------------------------------------------------ Pi generation
+__device__ __forceinline__ float to_tf32(float x) {
+    uint32_t y;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+    return __uint_as_float(y);
+}
+
+// pi[a][t] (ld = ldp) = Pi(a, row0 + t) rounded to TF32 for a < k, t < nrows; 0 for k <= a < kpad or
+// nrows <= t < tpad. One thread per (t, group of four sketch rows): one Philox block feeds four rows.
+__global__ void __launch_bounds__(256) pi_gen_kernel(float* __restrict__ pi, int64_t ldp, int k, int kpad,
+                                                     int64_t row0, int64_t nrows, int64_t tpad, uint32_t k0,
+                                                     uint32_t k1, float scale) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = blockIdx.y;
+    if (t >= tpad) return;
+    float z[4] = {0.f, 0.f, 0.f, 0.f};
+    if (t < nrows && 4 * g < k) {
+        const uint64_t row = (uint64_t)(row0 + t);
+        const U32x4 x = philox4x32_10((uint32_t)row, (uint32_t)(row >> 32), (uint32_t)g, TAG_PI, k0, k1);
+        box_muller_f32(x.x, x.y, z[0], z[1]);
+        box_muller_f32(x.z, x.w, z[2], z[3]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) z[q] = (4 * g + q < k) ? to_tf32(z[q] * scale) : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (4 * g + q < kpad) pi[(int64_t)(4 * g + q) * ldp + t] = z[q];
+}
+
+// ------------------------------------------------------------------------------------------------ main kernel
+struct TcArgs {
+    int64_t n1, n2, ntot;
+    int tiles_a;            // column tiles over A; tiles over B follow
+    int k, kc, nh;          // sketch rows, TMEM columns used (multiple of 32), Pi boxes per stage
+    int n_last;             // N of the last Pi box's MMA (multiple of 16)
+    uint32_t tmem_cols;     // power of two >= kc
+    int64_t nrows, rows_per_split;
+    int64_t ldk;
+    float* part;            // [splits][ntot][ldk]
+    double* nsq;            // [splits][ntot]
+    int* err;
+};
+
+__global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_constant__ CUtensorMap tm_a,
+                                                               const __grid_constant__ CUtensorMap tm_b,
+                                                               const __grid_constant__ CUtensorMap tm_pi,
+                                                               const TcArgs args) {
+    extern __shared__ uint8_t smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int split = blockIdx.y;
+    const int64_t rs = (int64_t)split * args.rows_per_split;
+    const int64_t re = min(args.nrows, rs + args.rows_per_split);
+    if (rs >= re) return;
+    const int n_it = (int)((re - rs + KS - 1) / KS);
+
+    const int tile = blockIdx.x;
+    const bool on_b = tile >= args.tiles_a;
+    const int64_t col0 = on_b ? (int64_t)(tile - args.tiles_a) * TILE_M : (int64_t)tile * TILE_M;
+    const int64_t ncols_src = on_b ? args.n2 : args.n1;
+    const int valid = (int)(ncols_src - col0 < TILE_M ? ncols_src - col0 : TILE_M);
+    const int64_t cbase = on_b ? args.n1 + col0 : col0;
+    const CUtensorMap* tm_data = on_b ? &tm_b : &tm_a;
+
+    // carve shared memory: stages (1024-byte aligned), then barriers
+    const uint32_t raw = smem_addr(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* base_ptr = smem_raw + (base - raw);
+    const uint32_t bar_base = base + STAGES * STAGE_BYTES;
+    uint64_t* bars = (uint64_t*)(base_ptr + STAGES * STAGE_BYTES);
+    // bars: [0, S) TMA full, [S, 2S) stage empty, [2S, 3S) K-major copy ready, [3S] accumulator ready; then the
+    // TMEM address word and the abort flag
+    uint32_t* tmem_slot = (uint32_t*)(bars + 3 * STAGES + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    auto full_bar = [&](int s) { return bar_base + 8u * s; };
+    auto empty_bar = [&](int s) { return bar_base + 8u * (STAGES + s); };
+    auto afull_bar = [&](int s) { return bar_base + 8u * (2 * STAGES + s); };
+    const uint32_t acc_bar = bar_base + 8u * (3 * STAGES);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);       // the MMA commit (the copy warps finished before the MMA started)
+            mbar_init(afull_bar(s), 4);       // four copy warps
+        }
+        mbar_init(acc_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(smem_addr(tmem_slot), args.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- TMA producer (the whole warp walks the ring; lane 0 issues)
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)tm_data) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_pi) : "memory");
+        }
+        const uint32_t bytes = DATA_STAGE_BYTES + args.nh * PI_BOX_BYTES;
+        for (int it = 0; it < n_it; ++it) {
+            const int s = it % STAGES;
+            const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+            bool ok = true;
+            if (it >= STAGES) ok = __all_sync(0xffffffffu, mbar_wait(empty_bar(s), ph ^ 1u, abort_flag));
+            if (!ok) {
+                if (lane == 0) {
+                    *abort_flag = 1;
+                    set_error(args.err, DEVERR_TIMEOUT | (1 << 8));
+                }
+                break;
+            }
+            if (lane == 0) {
+                mbar_arrive_expect_tx(full_bar(s), bytes);
+                const int t = (int)(rs + (int64_t)it * KS);
+                const uint32_t dst = base + s * STAGE_BYTES;
+#pragma unroll
+                for (int g = 0; g < KS / 8; ++g)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b)
+                        tma_load_2d(dst + g * KGROUP_BYTES + b * DATA_BOX_BYTES, tm_data, (int)col0 + 32 * b,
+                                    t + 8 * g, full_bar(s));
+                for (int h = 0; h < args.nh; ++h)
+                    tma_load_2d(dst + PI_OFF + h * PI_BOX_BYTES, &tm_pi, t, h * PI_BOX_ROWS, full_bar(s));
+            }
+            __syncwarp();
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (the whole warp waits; lane 0 issues)
+        const uint32_t id_full = idesc_tf32(TILE_M, PI_BOX_ROWS);
+        const uint32_t id_last = idesc_tf32(TILE_M, args.n_last);
+        bool ok = true;
+        for (int it = 0; it < n_it; ++it) {
+            const int s = it % STAGES;
+            const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+            // Pi arrives by TMA (full), the K-major data copy from the copy warps (afull)
+            ok = __all_sync(0xffffffffu, mbar_wait(full_bar(s), ph, abort_flag) && mbar_wait(afull_bar(s), ph, abort_flag));
+            if (!ok) {
+                if (lane == 0) {
+                    *abort_flag = 1;
+                    set_error(args.err, DEVERR_TIMEOUT | (1 << 9));
+                }
+                break;
+            }
+            tc_fence_after();
+            if (lane == 0) {
+                const uint32_t dbase = base + s * STAGE_BYTES;
+#pragma unroll
+                for (int kb = 0; kb < KS / 8; ++kb) {
+                    // both operands K-major, 64B swizzle: rows of 64 B, 8-row groups 512 B apart (SBO), K slice at +32 B
+                    const uint64_t ad = smem_desc(dbase + A_OFF + kb * 32, 16, 512, SWZ_64B);
+                    for (int h = 0; h < args.nh; ++h) {
+                        const uint64_t bd = smem_desc(dbase + PI_OFF + h * PI_BOX_BYTES + kb * 32, 16, 512, SWZ_64B);
+                        mma_tf32(tmem + h * PI_BOX_ROWS, ad, bd, h == args.nh - 1 ? id_last : id_full,
+                                 (it > 0 || kb > 0) ? 1u : 0u);
+                    }
+                }
+                mma_commit(empty_bar(s));
+            }
+            __syncwarp();
+        }
+        if (ok && lane == 0) mma_commit(acc_bar);
+        __syncwarp();
+    } else if (warp >= 4) {
+        // ---------------- column sums of squares (one 32-column box per warp), then the TMEM drain
+        const int box = warp - 4;
+        float hi = 0.f, lo = 0.f;
+        for (int it = 0; it < n_it; ++it) {
+            const int s = it % STAGES;
+            const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(full_bar(s), ph, abort_flag));
+            if (!ok) {
+                if (lane == 0) {
+                    *abort_flag = 1;
+                    set_error(args.err, DEVERR_TIMEOUT | (1 << 10));
+                }
+                break;
+            }
+            const float* stage_p = (const float*)(base_ptr + s * STAGE_BYTES);
+            // staged tile: 128B swizzle, the 16-byte chunk q of row t of a box sits at chunk q ^ (t & 7)
+            float x[KS];
+#pragma unroll
+            for (int t = 0; t < KS; ++t) {
+                const float* box_p = stage_p + ((t >> 3) * KGROUP_BYTES + box * DATA_BOX_BYTES) / 4;
+                const int tr = t & 7;
+                x[t] = box_p[tr * 32 + (((lane >> 2) ^ tr) << 2) + (lane & 3)];
+                two_sum_square<float>(x[t], hi, lo);
+            }
+            // K-major copy: data column m is row m (64 B = KS values); 64B swizzle puts chunk q at q ^ ((m >> 1) & 3)
+            const int m = box * 32 + lane;
+            float4* arow = (float4*)(base_ptr + s * STAGE_BYTES + A_OFF + m * (KS * 4));
+#pragma unroll
+            for (int q = 0; q < KS / 4; ++q)
+                arow[q ^ ((m >> 1) & 3)] =
+                    make_float4(to_tf32(x[4 * q]), to_tf32(x[4 * q + 1]), to_tf32(x[4 * q + 2]), to_tf32(x[4 * q + 3]));
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(afull_bar(s));
+        }
+        const int m = box * 32 + lane;   // TMEM lane = local data column
+        const bool acc_ok = __all_sync(0xffffffffu, !*abort_flag && mbar_wait(acc_bar, 0, abort_flag));
+        if (acc_ok) {
+            tc_fence_after();
+            const int64_t c = cbase + m;
+            float* dst = args.part + ((int64_t)split * args.ntot + c) * args.ldk;
+            for (int cc = 0; cc < args.kc; cc += 32) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(box * 32) << 16) + (uint32_t)cc, v);
+                if (m < valid) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (cc + i < args.k) dst[cc + i] += v[i];
+                }
+            }
+            if (m < valid) args.nsq[(int64_t)split * args.ntot + c] += (double)hi + (double)lo;
+        } else if (lane == 0) {
+            *abort_flag = 1;
+            set_error(args.err, DEVERR_TIMEOUT | (1 << 11));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, args.tmem_cols);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------ host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+// 2-D fp32 tensor map: inner extent `inner` (contiguous), `outer` rows of `ld` floats, box {box_inner, box_outer}.
+bool make_map(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer, uint64_t ld, uint32_t box_inner,
+              uint32_t box_outer, CUtensorMapSwizzle swz) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {inner, outer};
+    const cuuint64_t strides[1] = {ld * 4};
+    const cuuint32_t box[2] = {box_inner, box_outer};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool aligned16(const void* p, int64_t ld) { return ((uintptr_t)p % 16 == 0) && (ld % 4 == 0); }
+
+}  // namespace
+
+bool tc_supported(const smp_ctx* c) { return c->p.dtype == SMP_F32 && c->p.k <= MAX_KC && encode_fn() != nullptr; }
+
+bool tc_block_ok(const smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb) {
+    return tc_supported(c) && aligned16(A, lda) && (c->p.same_ab || aligned16(B, ldb));
+}
+
+cudaError_t launch_sketch_tc_pi(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t row0,
+                                int64_t nrows, const float* Pi, int64_t ldp) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int k = c->p.k;
+    const int kc = (int)round_up(k, 32);                 // TMEM columns drained (multiple of 32)
+    const int kmma = (int)round_up(k, 16);               // MMA N coverage
+    const int nh = (kmma + PI_BOX_ROWS - 1) / PI_BOX_ROWS;
+    const int n_last = kmma - (nh - 1) * PI_BOX_ROWS;
+    const int64_t tpad = round_up(nrows, KS);
+    cudaStream_t st = c->stream;
+    const float* pi = Pi;
+    int64_t pld = ldp;
+    int64_t pi_rows = k;
+    if (!pi) {
+        // generated Pi buffer: kpad rows (zero beyond k) x ld = round_up(max_rows, KS) columns
+        const int64_t ld = round_up(c->max_rows, KS);
+        const int kpad = nh * PI_BOX_ROWS;
+        const size_t need = (size_t)kpad * ld * 4;
+        if (c->tc_ws_bytes < need) {
+            if (c->tc_ws) cudaFree(c->tc_ws);
+            c->tc_ws = nullptr;
+            c->tc_ws_bytes = 0;
+            cudaError_t e = cudaMalloc(&c->tc_ws, need);
+            if (e != cudaSuccess) return e;
+            c->tc_ws_bytes = need;
+        }
+        const dim3 g((unsigned)((tpad + 255) / 256), (unsigned)(kpad / 4));
+        pi_gen_kernel<<<smp::counted(g), 256, 0, st>>>((float*)c->tc_ws, ld, k, kpad, row0, nrows, tpad,
+                                                       (uint32_t)c->p.seed, (uint32_t)(c->p.seed >> 32),
+                                                       (float)(1.0 / std::sqrt((double)k)));
+        pi = (const float*)c->tc_ws;
+        pld = ld;
+        pi_rows = kpad;
+    }
+    CUtensorMap ma, mb, mp;
+    const void* Bp = c->p.same_ab ? A : B;
+    const int64_t n2 = c->p.same_ab ? 0 : c->p.n2;
+    // data boxes: 32 columns (128 B, one swizzle row) x 8 rows = DATA_BOX_BYTES, matching the kernel's expect_tx
+    if (!make_map(&ma, A, (uint64_t)c->p.n1, (uint64_t)nrows, (uint64_t)lda, 32, DATA_BOX_ROWS, CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !make_map(&mb, Bp, (uint64_t)(c->p.same_ab ? c->p.n1 : c->p.n2), (uint64_t)nrows,
+                  (uint64_t)(c->p.same_ab ? lda : ldb), 32, DATA_BOX_ROWS,
+                  CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !make_map(&mp, pi, (uint64_t)(Pi ? nrows : tpad), (uint64_t)pi_rows, (uint64_t)pld, KS, PI_BOX_ROWS,
+                  CU_TENSOR_MAP_SWIZZLE_64B))
+        return cudaErrorInvalidValue;
+    TcArgs a;
+    a.n1 = c->p.n1;
+    a.n2 = n2;
+    a.ntot = c->ntot;
+    a.tiles_a = (int)((c->p.n1 + TILE_M - 1) / TILE_M);
+    const int tiles = a.tiles_a + (int)((n2 + TILE_M - 1) / TILE_M);
+    a.k = k;
+    a.kc = kc;
+    a.nh = nh;
+    a.n_last = n_last;
+    uint32_t cols = 32;
+    while ((int)cols < kc) cols <<= 1;
+    a.tmem_cols = cols;
+    a.nrows = nrows;
+    const int64_t steps = tpad / KS;
+    int splits = std::max(1, std::min(c->splits, c->sm_count / std::max(1, tiles)));
+    splits = (int)std::min<int64_t>(splits, steps);
+    a.rows_per_split = ((steps + splits - 1) / splits) * KS;
+    a.ldk = c->ldk;
+    a.part = (float*)c->part;
+    a.nsq = c->nsq;
+    a.err = c->dev_err;
+    sketch_tc_kernel<<<smp::counted(dim3((unsigned)tiles, (unsigned)splits)), THREADS, SMEM_BYTES, st>>>(ma, mb, mp, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_tc(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t row0,
+                             int64_t nrows) {
+    return launch_sketch_tc_pi(c, A, lda, B, ldb, row0, nrows, nullptr, 0);
 }
 
 }  // namespace smp
