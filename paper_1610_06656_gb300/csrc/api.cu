@@ -55,6 +55,7 @@ namespace {
 void free_ctx(smp_ctx* c) {
     void* ptrs[] = {c->part,   c->nsq,    c->sk,      c->s_all,   c->D_all,   c->F,     c->row_ptr, c->col_ptr,
                     c->col,    c->qhat,   c->csc_row, c->csc_pos, c->alpha,   c->beta,  c->mask,    c->wpre,
+                    c->erow,
                     c->row_cnt, c->col_cnt, c->dev_err, c->tc_ws};
     for (void* p : ptrs)
         if (p) cudaFree(p);

@@ -124,4 +124,37 @@ __device__ __forceinline__ void set_error(int* err, int bit) {
     if (err) atomicOr(err, bit);
 }
 
+// 1/sqrt(d) in binary64 without the long-latency binary64 square root and divide: the binary32 hardware estimate
+// (rsqrt.approx, relative error < 2^-22) refined by two Newton-Raphson steps y <- y (3 - d y^2) / 2, each of which
+// squares the relative error (2^-44, then below binary64 rounding). Falls back to 1 / sqrt(d) outside the binary32
+// range. d must be > 0.
+__device__ __forceinline__ double rsqrt_refined(double d) {
+    if (!(d > 1e-36 && d < 1e36)) return 1.0 / sqrt(d);
+    float yf;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"((float)d));
+    double y = (double)yf;
+    const double hd = 0.5 * d;
+    y = y * fma(-hd * y, y, 1.5);
+    y = y * fma(-hd * y, y, 1.5);
+    return y;
+}
+
+// Sum of 32 per-lane vectors: afterwards lane l holds sum over lanes of v[l]. Five butterfly rounds; in the round
+// with offset o each lane keeps the half of its live values selected by bit o of its lane id and adds the
+// partner's matching half (o shuffles per round, 31 in total).
+template <typename T>
+__device__ __forceinline__ T transpose_sum32(T (&v)[32], int lane) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const T send = upper ? v[i] : v[i + o];
+            const T keep = upper ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0];
+}
+
 }  // namespace smp

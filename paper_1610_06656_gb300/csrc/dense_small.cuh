@@ -1,64 +1,61 @@
-// Small dense binary64 kernels used by WAltMin's initial SVD and the canonical form: tall-skinny Gram matrices
-// with a fixed-order reduction, Cholesky of a b x b Gram (one warp), right-multiplication by R^-1, and a
-// parallel-order (round-robin pairing) cyclic Jacobi eigensolver for symmetric matrices of order <= 72.
+// Small dense kernels used by WAltMin's initial SVD and the canonical form: tall-skinny Gram matrices with a
+// fixed-order reduction, Cholesky of a b x b Gram (one warp), right-multiplication by R^-1, and a parallel-order
+// (round-robin pairing) cyclic Jacobi eigensolver for symmetric matrices of order <= 72.
+//
+// Binary64 divide and square root are long-latency instruction sequences on this part (hundreds of cycles), so
+// the binary64 code paths use rsqrt_refined (binary32 estimate + Newton-Raphson) and multiply by reciprocals.
 #pragma once
 #include "common.cuh"
 
 namespace smp {
 
-constexpr int GRAM_ROWS_PER_BLOCK = 256;
+constexpr int GRAM_ROWS_PER_BLOCK = 16;
 constexpr int MAX_SMALL = 72;   // largest order of the small dense problems (block size 2r + 8, r <= 32)
-constexpr int GRAM_STAGE = 16;
 
 // part[blk][p][q] = sum over this block's rows of X[i][p] * Y[i][q] (X: n x a, Y: n x b, row-major, ld = a / b).
 template <typename TX, typename TY>
 __global__ void __launch_bounds__(256) gram_partial_kernel(const TX* __restrict__ X, const TY* __restrict__ Y,
                                                            int64_t n, int a, int b, double* part) {
-    __shared__ double xs[GRAM_STAGE][MAX_SMALL + 1];
-    __shared__ double ys[GRAM_STAGE][MAX_SMALL + 1];
+    __shared__ double xs[GRAM_ROWS_PER_BLOCK][MAX_SMALL + 1];
+    __shared__ double ys[GRAM_ROWS_PER_BLOCK][MAX_SMALL + 1];
     const int64_t r0 = (int64_t)blockIdx.x * GRAM_ROWS_PER_BLOCK;
     const int64_t r1 = min(n, r0 + GRAM_ROWS_PER_BLOCK);
-    const int npair = a * b;
-    double acc[MAX_SMALL * MAX_SMALL / 256 + 1];
-    const int nmine = (npair + 255 - threadIdx.x) / 256;
-    for (int e = 0; e < nmine; ++e) acc[e] = 0.0;
-    for (int64_t base = r0; base < r1; base += GRAM_STAGE) {
-        const int rows = (int)(r1 - base < GRAM_STAGE ? r1 - base : GRAM_STAGE);
-        for (int e = threadIdx.x; e < GRAM_STAGE * a; e += blockDim.x) {
-            const int rr = e / a, cc = e - rr * a;
-            xs[rr][cc] = rr < rows ? (double)X[(base + rr) * a + cc] : 0.0;
-        }
-        for (int e = threadIdx.x; e < GRAM_STAGE * b; e += blockDim.x) {
-            const int rr = e / b, cc = e - rr * b;
-            ys[rr][cc] = rr < rows ? (double)Y[(base + rr) * b + cc] : 0.0;
-        }
-        __syncthreads();
-        for (int e = 0; e < nmine; ++e) {
-            const int pq = threadIdx.x + 256 * e;
-            const int p = pq / b, q = pq - p * b;
-            double s = acc[e];
-            for (int rr = 0; rr < rows; ++rr) s = fma(xs[rr][p], ys[rr][q], s);
-            acc[e] = s;
-        }
-        __syncthreads();
+    const int rows = (int)(r1 - r0);
+    for (int e = threadIdx.x; e < GRAM_ROWS_PER_BLOCK * a; e += blockDim.x) {
+        const int rr = e / a, cc = e - rr * a;
+        xs[rr][cc] = rr < rows ? (double)X[(r0 + rr) * a + cc] : 0.0;
     }
-    for (int e = 0; e < nmine; ++e) part[(int64_t)blockIdx.x * npair + threadIdx.x + 256 * e] = acc[e];
+    for (int e = threadIdx.x; e < GRAM_ROWS_PER_BLOCK * b; e += blockDim.x) {
+        const int rr = e / b, cc = e - rr * b;
+        ys[rr][cc] = rr < rows ? (double)Y[(r0 + rr) * b + cc] : 0.0;
+    }
+    __syncthreads();
+    const int npair = a * b;
+    for (int pq = threadIdx.x; pq < npair; pq += blockDim.x) {
+        const int p = pq / b, q = pq - p * b;
+        double s = 0.0;
+        for (int rr = 0; rr < rows; ++rr) s = fma(xs[rr][p], ys[rr][q], s);
+        part[(int64_t)blockIdx.x * npair + pq] = s;
+    }
 }
 
-// G[pq] = sum over blocks (in order) of part[blk][pq].
+// G[pq] = sum over blocks of part[blk][pq]: one warp per entry, lane-strided partial sums then a fixed shuffle
+// tree (deterministic).
 __global__ void gram_reduce_kernel(const double* __restrict__ part, int nblk, int npair, double* G) {
-    const int pq = blockIdx.x * blockDim.x + threadIdx.x;
+    const int pq = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (pq >= npair) return;
     double s = 0.0;
-    for (int k = 0; k < nblk; ++k) s += part[(int64_t)k * npair + pq];
-    G[pq] = s;
+    for (int k = lane; k < nblk; k += 32) s += part[(int64_t)k * npair + pq];
+    s = warp_sum(s);
+    if (lane == 0) G[pq] = s;
 }
 
 // Upper Cholesky factor R (G = R^T R) of a b x b symmetric matrix by one warp. A pivot <= tol * max diag marks a
-// rank-deficient direction: that row of R is zeroed (apply_rinv then zeroes the column) and the flag is counted.
-__global__ void chol_kernel(const double* __restrict__ G, int b, double* R, double tol, int* ndropped) {
+// rank-deficient direction: that row of R is zeroed (apply_rinv then zeroes the column).
+__global__ void chol_kernel(const double* __restrict__ G, int b, double* R, double tol) {
     __shared__ double L[MAX_SMALL][MAX_SMALL + 1];
-    __shared__ double dj;
+    __shared__ double rinv_j;
     const int lane = threadIdx.x;
     double maxd = 0.0;
     for (int e = lane; e < b * b; e += 32) {
@@ -69,17 +66,17 @@ __global__ void chol_kernel(const double* __restrict__ G, int b, double* R, doub
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) maxd = fmax(maxd, __shfl_xor_sync(0xffffffffu, maxd, o));
     __syncwarp();
-    int dropped = 0;
     for (int j = 0; j < b; ++j) {
         if (lane == 0) {
             const double d = L[j][j];
-            dj = (d > tol * maxd && d > 0.0) ? sqrt(d) : 0.0;
-            L[j][j] = dj;
+            const bool ok = d > tol * maxd && d > 0.0;
+            const double y = ok ? rsqrt_refined(d) : 0.0;
+            L[j][j] = ok ? d * y : 0.0;
+            rinv_j = y;
         }
         __syncwarp();
-        const double d = dj;
-        if (d == 0.0) ++dropped;
-        for (int i = j + 1 + lane; i < b; i += 32) L[i][j] = d > 0.0 ? L[i][j] / d : 0.0;
+        const double y = rinv_j;
+        for (int i = j + 1 + lane; i < b; i += 32) L[i][j] *= y;
         __syncwarp();
         for (int i = j + 1 + lane; i < b; i += 32) {
             const double lij = L[i][j];
@@ -87,54 +84,77 @@ __global__ void chol_kernel(const double* __restrict__ G, int b, double* R, doub
         }
         __syncwarp();
     }
-    // R = L^T (upper)
     for (int e = lane; e < b * b; e += 32) {
         const int i = e / b, j = e - i * b;
         R[e] = j >= i ? L[j][i] : 0.0;
     }
-    if (lane == 0 && ndropped) *ndropped = dropped;
 }
 
-// X_out[i] = X_in[i] R^-1 (row vector times inverse upper factor); a zero pivot zeroes that column.
-template <typename TIn, typename TOut>
+// X_out[i] = X_in[i] R^-1 (row vector times inverse upper factor), the substitution carried out in TC (binary32
+// for the subspace iteration's first Cholesky-QR pass, whose second pass restores orthogonality; binary64 for the
+// canonical form); a zero pivot zeroes that column.
+template <typename TIn, typename TOut, typename TC>
 __global__ void __launch_bounds__(128) apply_rinv_kernel(const TIn* __restrict__ Xin, int64_t n, int b,
                                                          const double* __restrict__ R, TOut* Xout) {
-    __shared__ double Rs[MAX_SMALL * MAX_SMALL];
-    for (int e = threadIdx.x; e < b * b; e += blockDim.x) Rs[e] = R[e];
+    __shared__ TC Rs[MAX_SMALL * MAX_SMALL];
+    __shared__ TC dinv[MAX_SMALL];
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) Rs[e] = (TC)R[e];
+    for (int j = threadIdx.x; j < b; j += blockDim.x) {
+        const double d = R[j * b + j];
+        dinv[j] = d > 0.0 ? (TC)rsqrt_refined(d * d) : TC(0);
+    }
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double x[MAX_SMALL];
+    TC x[MAX_SMALL];
     for (int j = 0; j < b; ++j) {
-        double y = (double)Xin[i * b + j];
+        TC y = (TC)Xin[i * b + j];
         for (int l = 0; l < j; ++l) y -= x[l] * Rs[l * b + j];
-        const double d = Rs[j * b + j];
-        x[j] = d != 0.0 ? y / d : 0.0;
+        x[j] = y * dinv[j];
     }
     for (int j = 0; j < b; ++j) Xout[i * b + j] = (TOut)x[j];
 }
 
-// Symmetric eigen decomposition A = V diag(lambda) V^T (n <= MAX_SMALL) by cyclic Jacobi with round-robin pairing
-// (n/2 disjoint rotations per step, all applied in parallel). Rotation in the (p, q) plane with
-// theta = (A_qq - A_pp) / (2 A_pq), t = sign(theta) / (|theta| + sqrt(theta^2 + 1)), c = 1/sqrt(1 + t^2), s = t c
-// zeroes A_pq. Stops when the off-diagonal square sum (summed directly) is <= tol^2 times the diagonal's.
-// Output: eigenvalues in decreasing order and V's columns permuted to match. One CTA of 256 threads, dynamic
-// shared memory 2 * n * (n + 1) doubles.
+// Rotation (c, s) in the (p, q) plane that zeroes A_pq: theta = (A_qq - A_pp) / (2 A_pq),
+// t = sign(theta) / (|theta| + sqrt(theta^2 + 1)), c = 1 / sqrt(1 + t^2), s = t c. The binary64 version takes t
+// from binary32 arithmetic (the angle only steers convergence) and c from rsqrt_refined, so c^2 + s^2 = 1 to
+// binary64 rounding and the accumulated V stays orthogonal.
+__device__ __forceinline__ void jacobi_rotation(float app, float aqq, float apq, float& c, float& s) {
+    const float th = (aqq - app) / (2.0f * apq);
+    float t = 0.0f;
+    if (isfinite(th)) t = (th >= 0.0f ? 1.0f : -1.0f) / (fabsf(th) + sqrtf(fmaf(th, th, 1.0f)));
+    c = rsqrtf(fmaf(t, t, 1.0f));
+    s = t * c;
+}
+__device__ __forceinline__ void jacobi_rotation(double app, double aqq, double apq, double& c, double& s) {
+    const float thf = (float)(aqq - app) / (2.0f * (float)apq);
+    float tf = 0.0f;
+    if (isfinite(thf)) tf = (thf >= 0.0f ? 1.0f : -1.0f) / (fabsf(thf) + sqrtf(fmaf(thf, thf, 1.0f)));
+    const double t = (double)tf;
+    c = rsqrt_refined(fma(t, t, 1.0));
+    s = t * c;
+}
+
+// Symmetric eigen decomposition A = V diag(lambda) V^T (n <= MAX_SMALL) in precision T by cyclic Jacobi with
+// round-robin pairing (n/2 disjoint rotations per step, all applied in parallel). Stops when the off-diagonal
+// square sum (summed directly) is <= tol^2 times the diagonal's. Output (binary64): eigenvalues in decreasing
+// order and V's columns permuted to match. One CTA of 256 threads, dynamic shared memory 2 n (n + 1) sizeof(T).
+template <typename T>
 __global__ void __launch_bounds__(256) jacobi_eig_kernel(const double* __restrict__ Ain, int n, double tol,
                                                          int max_sweeps, double* evals, double* Vout) {
-    extern __shared__ double sm[];
-    double* A = sm;                  // n x (n+1)
-    double* V = sm + n * (n + 1);    // n x (n+1)
+    extern __shared__ __align__(16) unsigned char jsm[];
+    T* A = (T*)jsm;                  // n x (n+1)
+    T* V = A + n * (n + 1);          // n x (n+1)
     __shared__ int rp[MAX_SMALL / 2 + 1], rq[MAX_SMALL / 2 + 1];
-    __shared__ double rc[MAX_SMALL / 2 + 1], rs[MAX_SMALL / 2 + 1];
-    __shared__ double red[8];
+    __shared__ T rc[MAX_SMALL / 2 + 1], rs[MAX_SMALL / 2 + 1];
+    __shared__ double red[8], red2[8];
     __shared__ int stop;
     __shared__ int order[MAX_SMALL];
     const int ld = n + 1;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int i = e / n, j = e - i * n;
-        A[i * ld + j] = Ain[e];
-        V[i * ld + j] = i == j ? 1.0 : 0.0;
+        A[i * ld + j] = (T)Ain[e];
+        V[i * ld + j] = i == j ? T(1) : T(0);
     }
     __syncthreads();
     const int m = n + (n & 1);
@@ -143,28 +163,24 @@ __global__ void __launch_bounds__(256) jacobi_eig_kernel(const double* __restric
         double off = 0.0, dia = 0.0;
         for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
             const int i = e / n, j = e - i * n;
-            const double v = A[i * ld + j];
+            const double v = (double)A[i * ld + j];
             if (i == j) dia += v * v;
             else off += v * v;
         }
         off = warp_sum(off);
         dia = warp_sum(dia);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = off;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double o = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) o += red[w];
-            red[0] = o;
+        if ((threadIdx.x & 31) == 0) {
+            red[threadIdx.x >> 5] = off;
+            red2[threadIdx.x >> 5] = dia;
         }
         __syncthreads();
-        const double off_total = red[0];
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dia;
-        __syncthreads();
         if (threadIdx.x == 0) {
-            double d = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) d += red[w];
-            stop = off_total <= tol * tol * d;
+            double o = 0.0, d = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                o += red[w];
+                d += red2[w];
+            }
+            stop = o <= tol * tol * d;
         }
         __syncthreads();
         if (stop) break;
@@ -179,15 +195,10 @@ __global__ void __launch_bounds__(256) jacobi_eig_kernel(const double* __restric
                     p = q;
                     q = t;
                 }
-                double c = 1.0, sn = 0.0;
+                T c = T(1), sn = T(0);
                 if (q < n) {
-                    const double apq = A[p * ld + q];
-                    if (apq != 0.0) {
-                        const double th = (A[q * ld + q] - A[p * ld + p]) / (2.0 * apq);
-                        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-                        c = 1.0 / sqrt(t * t + 1.0);
-                        sn = t * c;
-                    }
+                    const T apq = A[p * ld + q];
+                    if (apq != T(0)) jacobi_rotation(A[p * ld + p], A[q * ld + q], apq, c, sn);
                 } else {
                     q = p;   // dummy player: no rotation
                 }
@@ -197,40 +208,37 @@ __global__ void __launch_bounds__(256) jacobi_eig_kernel(const double* __restric
                 rs[k] = sn;
             }
             __syncthreads();
-            // columns of A and V
-            for (int e = threadIdx.x; e < npairs * n; e += blockDim.x) {
+            for (int e = threadIdx.x; e < npairs * n; e += blockDim.x) {   // columns of A and V
                 const int k = e / n, i = e - k * n;
                 const int p = rp[k], q = rq[k];
                 if (p == q) continue;
-                const double c = rc[k], sn = rs[k];
-                const double ap = A[i * ld + p], aq = A[i * ld + q];
+                const T c = rc[k], sn = rs[k];
+                const T ap = A[i * ld + p], aq = A[i * ld + q];
                 A[i * ld + p] = c * ap - sn * aq;
                 A[i * ld + q] = sn * ap + c * aq;
-                const double vp = V[i * ld + p], vq = V[i * ld + q];
+                const T vp = V[i * ld + p], vq = V[i * ld + q];
                 V[i * ld + p] = c * vp - sn * vq;
                 V[i * ld + q] = sn * vp + c * vq;
             }
             __syncthreads();
-            // rows of A
-            for (int e = threadIdx.x; e < npairs * n; e += blockDim.x) {
+            for (int e = threadIdx.x; e < npairs * n; e += blockDim.x) {   // rows of A
                 const int k = e / n, i = e - k * n;
                 const int p = rp[k], q = rq[k];
                 if (p == q) continue;
-                const double c = rc[k], sn = rs[k];
-                const double ap = A[p * ld + i], aq = A[q * ld + i];
+                const T c = rc[k], sn = rs[k];
+                const T ap = A[p * ld + i], aq = A[q * ld + i];
                 A[p * ld + i] = c * ap - sn * aq;
                 A[q * ld + i] = sn * ap + c * aq;
             }
             __syncthreads();
         }
     }
-    // sort eigenvalues decreasing (stable: ties keep the lower index first)
-    if (threadIdx.x < n) {
+    if (threadIdx.x < n) {   // stable sort, decreasing
         const int i = threadIdx.x;
-        const double li = A[i * ld + i];
+        const T li = A[i * ld + i];
         int rank = 0;
         for (int j = 0; j < n; ++j) {
-            const double lj = A[j * ld + j];
+            const T lj = A[j * ld + j];
             rank += (lj > li) || (lj == li && j < i);
         }
         order[rank] = i;
@@ -238,9 +246,9 @@ __global__ void __launch_bounds__(256) jacobi_eig_kernel(const double* __restric
     __syncthreads();
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int i = e / n, c = e - i * n;
-        Vout[e] = V[i * ld + order[c]];
+        Vout[e] = (double)V[i * ld + order[c]];
     }
-    if (threadIdx.x < n) evals[threadIdx.x] = A[order[threadIdx.x] * ld + order[threadIdx.x]];
+    if (threadIdx.x < n) evals[threadIdx.x] = (double)A[order[threadIdx.x] * ld + order[threadIdx.x]];
 }
 
 }  // namespace smp

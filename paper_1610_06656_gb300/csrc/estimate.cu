@@ -1,65 +1,55 @@
 // Rescaled JL estimate over Omega (Algorithm 1, step 4; Eq. (2)), as a sampled dense-dense product (SDDMM):
 // M~(i, j) = D_A,i D_B,j <At_i, Bt_j>, the compact form D_A At^T Bt D_B with (D_X)_cc = ||X_c|| / ||Xt_c||
-// (Appendix B). One warp per CSR row i keeps At_i in registers and walks the row's columns; each Bt_j (k
-// contiguous values) is read with coalesced lane-strided loads from L2 and reduced with warp shuffles.
+// (Appendix B).
+//
+// Work is split by CSR position, not by row: rows of heavy columns keep every entry (q^ = 1 across the row) and
+// would otherwise serialise on one warp. Each warp takes CHUNK consecutive entries; it keeps At_i in registers
+// while the row index stays the same (rows are contiguous in CSR order), reads each Bt_j (k contiguous values)
+// with coalesced lane-strided loads from L2, reduces with warp shuffles, and scales in binary64.
 #include "common.cuh"
 #include "internal.h"
 
 namespace smp {
 namespace {
 
+constexpr int CHUNK = 8;
+
 template <typename T, int NPL>
 __global__ void __launch_bounds__(256) estimate_kernel(const T* __restrict__ At, const T* __restrict__ Bt,
                                                        int64_t ldk, int k, const double* __restrict__ DA,
                                                        const double* __restrict__ DB,
-                                                       const int64_t* __restrict__ row_ptr,
-                                                       const int32_t* __restrict__ col, int64_t n1, T* vals) {
+                                                       const int32_t* __restrict__ erow,
+                                                       const int32_t* __restrict__ col, int64_t nnz, T* vals) {
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (warp >= n1) return;
-    const int64_t i = warp;
+    const int64_t p0 = warp * CHUNK;
+    if (p0 >= nnz) return;
+    const int64_t p1 = min(nnz, p0 + CHUNK);
+    int64_t cur = -1;
+    double da = 0.0;
     T a[NPL];
-    const T* ai = At + i * ldk;
+    for (int64_t p = p0; p < p1; ++p) {
+        const int64_t i = erow[p];
+        if (i != cur) {
+            cur = i;
+            da = DA[i];
+            const T* ai = At + i * ldk;
 #pragma unroll
-    for (int q = 0; q < NPL; ++q) {
-        const int idx = lane + 32 * q;
-        a[q] = idx < k ? ai[idx] : T(0);
-    }
-    const double da = DA[i];
-    const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
-    int64_t p = p0;
-    // two columns per iteration for memory-level parallelism
-    for (; p + 1 < p1; p += 2) {
-        const int64_t j0 = col[p], j1 = col[p + 1];
-        const T* b0 = Bt + j0 * ldk;
-        const T* b1 = Bt + j1 * ldk;
-        T s0 = T(0), s1 = T(0);
-#pragma unroll
-        for (int q = 0; q < NPL; ++q) {
-            const int idx = lane + 32 * q;
-            if (idx < k) {
-                s0 = fma(a[q], b0[idx], s0);
-                s1 = fma(a[q], b1[idx], s1);
+            for (int q = 0; q < NPL; ++q) {
+                const int idx = lane + 32 * q;
+                a[q] = idx < k ? ai[idx] : T(0);
             }
         }
-        s0 = warp_sum(s0);
-        s1 = warp_sum(s1);
-        if (lane == 0) {
-            vals[p] = (T)(da * DB[j0] * (double)s0);
-            vals[p + 1] = (T)(da * DB[j1] * (double)s1);
-        }
-    }
-    if (p < p1) {
-        const int64_t j0 = col[p];
-        const T* b0 = Bt + j0 * ldk;
-        T s0 = T(0);
+        const int64_t j = col[p];
+        const T* bj = Bt + j * ldk;
+        T s = T(0);
 #pragma unroll
         for (int q = 0; q < NPL; ++q) {
             const int idx = lane + 32 * q;
-            if (idx < k) s0 = fma(a[q], b0[idx], s0);
+            if (idx < k) s = fma(a[q], bj[idx], s);
         }
-        s0 = warp_sum(s0);
-        if (lane == 0) vals[p] = (T)(da * DB[j0] * (double)s0);
+        s = warp_sum(s);
+        if (lane == 0) vals[p] = (T)(da * DB[j] * (double)s);
     }
 }
 
@@ -69,10 +59,10 @@ void launch_npl(smp_ctx* c, void* vals) {
     const T* Bt = c->p.same_ab ? At : At + c->p.n1 * c->ldk;
     const double* DA = c->D_all;
     const double* DB = c->p.same_ab ? c->D_all : c->D_all + c->p.n1;
-    const int64_t warps = c->p.n1;
+    const int64_t warps = (c->nnz + CHUNK - 1) / CHUNK;
     const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
-    estimate_kernel<T, NPL><<<smp::counted(blocks), 256, 0, c->stream>>>(At, Bt, c->ldk, c->p.k, DA, DB, c->row_ptr, c->col,
-                                                           c->p.n1, (T*)vals);
+    estimate_kernel<T, NPL><<<smp::counted(blocks), 256, 0, c->stream>>>(At, Bt, c->ldk, c->p.k, DA, DB, c->erow,
+                                                                         c->col, c->nnz, (T*)vals);
 }
 
 template <typename T>

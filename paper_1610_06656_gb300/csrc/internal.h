@@ -31,6 +31,7 @@ struct smp_ctx {
     int64_t* row_ptr = nullptr;     // [n1 + 1]
     int64_t* col_ptr = nullptr;     // [n2 + 1]
     int32_t* col = nullptr;         // [cap]
+    int32_t* erow = nullptr;        // [cap] row of each CSR entry
     double* qhat = nullptr;         // [cap]
     int32_t* csc_row = nullptr;     // [cap]
     int64_t* csc_pos = nullptr;     // [cap]

@@ -148,7 +148,7 @@ __global__ void scan_kernel(const int32_t* __restrict__ cnt, int64_t n, int64_t*
 __global__ void fill_csr_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ wpre,
                                 const int64_t* __restrict__ row_ptr, const double* __restrict__ alpha,
                                 const double* __restrict__ beta, int64_t n1, int64_t n2, int64_t W, int32_t* col,
-                                double* qhat) {
+                                int32_t* erow, double* qhat) {
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= n1 * W) return;
@@ -158,6 +158,7 @@ __global__ void fill_csr_kernel(const uint32_t* __restrict__ mask, const int32_t
     const int64_t j = w * 32 + lane;
     const int64_t pos = row_ptr[i] + wpre[warp] + __popc(bits & ((1u << lane) - 1u));
     col[pos] = (int32_t)j;
+    erow[pos] = (int32_t)i;
     qhat[pos] = qhat_of(alpha[i], beta[j]);
 }
 
@@ -255,16 +256,17 @@ smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out) {
         return check_cuda(c, e, "smp_sample nnz copy");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return check_cuda(c, e, "smp_sample sync");
     if (nnz > c->cap) {
-        int64_t have = c->cap, h2 = c->cap, h3 = c->cap, h4 = c->cap;
+        int64_t have = c->cap, h2 = c->cap, h3 = c->cap, h4 = c->cap, h5 = c->cap;
         const int64_t want = nnz + nnz / 8 + 1024;
         if (ensure(c->col, have, want) != cudaSuccess || ensure(c->qhat, h2, want) != cudaSuccess ||
-            ensure(c->csc_row, h3, want) != cudaSuccess || ensure(c->csc_pos, h4, want) != cudaSuccess)
+            ensure(c->csc_row, h3, want) != cudaSuccess || ensure(c->csc_pos, h4, want) != cudaSuccess ||
+            ensure(c->erow, h5, want) != cudaSuccess)
             return fail(c, SMP_ENOMEM, "smp_sample: cannot allocate Omega");
         c->cap = want;
     }
     if (nnz > 0) {
         fill_csr_kernel<<<smp::counted(blocks), 256, 0, st>>>(c->mask, c->wpre, c->row_ptr, c->alpha, c->beta, n1, n2, W, c->col,
-                                                c->qhat);
+                                                c->erow, c->qhat);
         fill_csc_kernel<<<smp::counted((unsigned)n2), 256, 0, st>>>(c->mask, c->wpre, c->row_ptr, c->col_ptr, n1, W, c->csc_row,
                                                       c->csc_pos);
         if ((e = cudaGetLastError()) != cudaSuccess) return check_cuda(c, e, "smp_sample fill kernels");

@@ -2,13 +2,18 @@
 //
 //  * weights w = 1/q^ (step 2); optional split of Omega into 2T+1 subsets by the split coin (step 3);
 //  * U0: top-r left singular subspace of R_Omega0(M~) = w .* P_Omega0(M~) (steps 4-5) by block subspace iteration
-//    with b = min(2r + 8, n1, n2) columns: Y <- orth(R (R^T Y)) with CSR / CSC sparse products and a Cholesky-QR
-//    (twice) in binary64, then a Rayleigh-Ritz step on Z = R^T Y; trim (step 6);
-//  * T rounds of the two weighted least-squares half-steps (steps 8 and 9): one warp per output row builds
-//    G = sum w f f^T and b = sum w M~ f with warp shuffles, adds the ridge 1e-10 tr(G)/r, and solves by a binary64
-//    Cholesky held in shared memory;
+//    with b = min(2r + 8, 72, n1, n2) columns: Y <- orth(R (R^T Y)) with entry-parallel CSR / CSC products and a
+//    Cholesky-QR (twice) whose factorisation runs in binary64, then a Rayleigh-Ritz step on Z = R^T Y; trim (6);
+//  * T rounds of the two weighted least-squares half-steps (steps 8 and 9). Each output row's samples are cut into
+//    segments of at most SEG entries; one warp per segment accumulates the partial Gram G = sum w f f^T and
+//    b = sum w M~ f (lane l owns column l of G); one thread per output row then sums its segments in binary64, adds
+//    the ridge 1e-10 tr(G)/r and solves by its own binary64 Cholesky;
 //  * canonical form: Cholesky-QR (twice) of U^ and V^, the SVD of the r x r core Ru Rv^T via the symmetric
 //    eigenproblem of [[0, K], [K^T, 0]], and the sign rule (largest-magnitude entry of each U column positive).
+//
+// Binary64 is used where the method needs it (the r x r and b x b factorisations, the canonical form); the
+// per-sample arithmetic stays in binary32 unless SMP_FP64_ALS asks otherwise, because binary64 throughput on this
+// part is about 1/40 of binary32.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -20,18 +25,13 @@
 namespace smp {
 namespace {
 
-constexpr int LS_WARPS = 4;
+constexpr int SEG = 64;          // samples per LS segment
+constexpr int LS_WARPS = 4;      // segments per CTA in the Gram kernel
+constexpr int CHECK_EVERY = 4;   // subspace-iteration steps between convergence checks
 
 // ---------------------------------------------------------------------------------------------------------------
 // weights, split, values of R_Omega(M~)
 // ---------------------------------------------------------------------------------------------------------------
-__global__ void erow_kernel(const int64_t* __restrict__ row_ptr, int64_t n1, int32_t* erow) {
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= n1) return;
-    for (int64_t p = row_ptr[warp] + lane; p < row_ptr[warp + 1]; p += 32) erow[p] = (int32_t)warp;
-}
-
 __global__ void split_kernel(const int32_t* __restrict__ erow, const int32_t* __restrict__ col, int64_t nnz, int T,
                              uint32_t k0, uint32_t k1, uint8_t* sub) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -41,15 +41,21 @@ __global__ void split_kernel(const int32_t* __restrict__ erow, const int32_t* __
     sub[e] = (uint8_t)min((int)f, 2 * T);
 }
 
+// rv[e] = w_e M~_e for entries of subset sid (0 elsewhere), in CSR order; rv_csc = the same values in CSC order.
 template <typename TV, typename TR>
 __global__ void rvals_kernel(const TV* __restrict__ vals, const double* __restrict__ qhat,
-                             const uint8_t* __restrict__ sub, int sid, int64_t nnz, TR* rv) {
+                             const uint8_t* __restrict__ sub, int sid, const int64_t* __restrict__ csc_pos,
+                             int64_t nnz, TR* rv, TR* rv_csc) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nnz) return;
-    const double q = qhat[e];
-    const double w = q > 0.0 ? 1.0 / q : 0.0;
-    const bool in = sub == nullptr || sub[e] == sid;
-    rv[e] = in ? (TR)(w * (double)vals[e]) : TR(0);
+    auto value = [&](int64_t p) {
+        const double q = qhat[p];
+        const double w = q > 0.0 ? 1.0 / q : 0.0;
+        const bool in = sub == nullptr || sub[p] == sid;
+        return in ? (TR)(w * (double)vals[p]) : TR(0);
+    };
+    rv[e] = value(e);
+    rv_csc[e] = value(csc_pos[e]);
 }
 
 // ---------------------------------------------------------------------------------------------------------------
@@ -71,45 +77,51 @@ __global__ void start_block_kernel(int64_t n1, int b, uint32_t k0, uint32_t k1, 
         if (4 * g + q < b) Y[i * b + 4 * g + q] = (TY)z[q];
 }
 
-// Y[i] = sum over row i of rv * Z[col]   (warp per row, lanes over the b columns)
-template <typename TY>
-__global__ void spmm_csr_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                                const TY* __restrict__ rv, const TY* __restrict__ Z, int64_t n1, int b, TY* Y) {
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// Partial sparse product of one segment: Yp[s] = sum over the segment's entries p of val[p] X[idx[p]] (lanes over
+// the b columns, BCH chunks of 32; the segment's indices and values are loaded once per 32 entries and broadcast).
+template <typename TY, int BCH>
+__global__ void __launch_bounds__(256) spmm_seg_kernel(const int64_t* __restrict__ seg_b,
+                                                       const int64_t* __restrict__ seg_e, int64_t nseg,
+                                                       const int32_t* __restrict__ idx, const TY* __restrict__ val,
+                                                       const TY* __restrict__ X, int b, TY* Yp) {
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (warp >= n1) return;
-    TY acc[3] = {TY(0), TY(0), TY(0)};
-    for (int64_t p = row_ptr[warp]; p < row_ptr[warp + 1]; ++p) {
-        const TY v = rv[p];
-        const TY* z = Z + (int64_t)col[p] * b;
+    if (s >= nseg) return;
+    TY acc[BCH];
 #pragma unroll
-        for (int q = 0; q < 3; ++q)
-            if (lane + 32 * q < b) acc[q] = fma(v, z[lane + 32 * q], acc[q]);
+    for (int h = 0; h < BCH; ++h) acc[h] = TY(0);
+    const int64_t p0 = seg_b[s], p1 = seg_e[s];
+    for (int64_t base = p0; base < p1; base += 32) {
+        const int64_t p = base + lane;
+        const int32_t in = p < p1 ? idx[p] : 0;
+        const TY v = p < p1 ? val[p] : TY(0);
+        const int cnt = (int)(p1 - base < 32 ? p1 - base : 32);
+#pragma unroll 4
+        for (int t = 0; t < cnt; ++t) {
+            const int32_t in_t = __shfl_sync(0xffffffffu, in, t);
+            const TY v_t = __shfl_sync(0xffffffffu, v, t);
+            const TY* x = X + (int64_t)in_t * b;
+#pragma unroll
+            for (int h = 0; h < BCH; ++h)
+                if (h * 32 + lane < b) acc[h] = fma(v_t, x[h * 32 + lane], acc[h]);
+        }
     }
 #pragma unroll
-    for (int q = 0; q < 3; ++q)
-        if (lane + 32 * q < b) Y[warp * b + lane + 32 * q] = acc[q];
+    for (int h = 0; h < BCH; ++h)
+        if (h * 32 + lane < b) Yp[s * b + h * 32 + lane] = acc[h];
 }
 
-// Z[j] = sum over column j of rv * Y[row]   (warp per column)
+// Y[o][c] = sum of the segment partials of row o, in segment order.
 template <typename TY>
-__global__ void spmm_csc_kernel(const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ csc_row,
-                                const int64_t* __restrict__ csc_pos, const TY* __restrict__ rv,
-                                const TY* __restrict__ Y, int64_t n2, int b, TY* Z) {
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= n2) return;
-    TY acc[3] = {TY(0), TY(0), TY(0)};
-    for (int64_t p = col_ptr[warp]; p < col_ptr[warp + 1]; ++p) {
-        const TY v = rv[csc_pos[p]];
-        const TY* y = Y + (int64_t)csc_row[p] * b;
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-            if (lane + 32 * q < b) acc[q] = fma(v, y[lane + 32 * q], acc[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-        if (lane + 32 * q < b) Z[warp * b + lane + 32 * q] = acc[q];
+__global__ void spmm_reduce_kernel(const int64_t* __restrict__ seg_start, const TY* __restrict__ Yp, int64_t n_out,
+                                   int b, TY* Y) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_out * b) return;
+    const int64_t o = e / b;
+    const int c = (int)(e - o * b);
+    TY acc = TY(0);
+    for (int64_t s = seg_start[o]; s < seg_start[o + 1]; ++s) acc += Yp[s * b + c];
+    Y[e] = acc;
 }
 
 // U0[i][c] = sum_l Y[i][l] E[l][c] for the top-r Ritz vectors (E: b x b, eigenvectors in columns, sorted).
@@ -148,29 +160,80 @@ __global__ void convert_kernel(const TA* __restrict__ a, int64_t n, TB* b) {
 // ---------------------------------------------------------------------------------------------------------------
 // weighted least-squares half-step
 // ---------------------------------------------------------------------------------------------------------------
-// For every output row o: x_o = argmin sum_{e in row o} w_e (F[idx_e] . x - M~_e)^2 over the entries of subset sid
-// (all entries when sub is null). ptr/idx walk CSR (pos = null) or CSC (pos maps to CSR positions, where vals,
-// qhat and sub live). Lane l holds column l of G; the factor row of each sample is loaded once (lane c -> F[c])
-// and broadcast with shuffles.
+// Segments: each output row o is cut into max(1, ceil(len / SEG)) pieces of at most SEG consecutive entries.
+__global__ void seg_count_kernel(const int64_t* __restrict__ ptr, int64_t n, int32_t* cnt) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    const int64_t len = ptr[o + 1] - ptr[o];
+    cnt[o] = (int32_t)(len > SEG ? (len + SEG - 1) / SEG : 1);
+}
+
+// Exclusive scan of n int32 counts into int64 offsets (out has n + 1 entries). One CTA, chunked, fixed order.
+__global__ void scan_kernel(const int32_t* __restrict__ cnt, int64_t n, int64_t* out) {
+    __shared__ int64_t wsum[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int64_t base = 0; base < n; base += blockDim.x) {
+        const int64_t idx = base + threadIdx.x;
+        const int64_t c = idx < n ? (int64_t)cnt[idx] : 0;
+        int64_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int64_t v = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            wsum[lane] = v;
+        }
+        __syncthreads();
+        const int64_t excl = x - c + (wid ? wsum[wid - 1] : 0) + carry;
+        if (idx < n) out[idx] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + c;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
+
+// Segment bounds: [seg_b, seg_e) for every segment of every output row.
+__global__ void seg_fill_kernel(const int64_t* __restrict__ ptr, const int64_t* __restrict__ seg_start, int64_t n,
+                                int64_t* seg_b, int64_t* seg_e) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    const int64_t s0 = seg_start[o], s1 = seg_start[o + 1];
+    for (int64_t s = s0; s < s1; ++s) {
+        const int64_t b0 = ptr[o] + (s - s0) * SEG;
+        seg_b[s] = b0;
+        seg_e[s] = min(ptr[o + 1], b0 + SEG);
+    }
+}
+
+// Partial Gram of one segment: lane l accumulates column l of G; each sample's factor row is loaded once
+// (lane c <- F[c]) and broadcast. part[s] = G (r x r, full) followed by b (r).
 template <typename TF, typename TG, typename TV, int RMAX>
-__global__ void __launch_bounds__(32 * LS_WARPS) ls_kernel(const int64_t* __restrict__ ptr,
-                                                           const int32_t* __restrict__ idx,
-                                                           const int64_t* __restrict__ pos,
-                                                           const TV* __restrict__ vals,
-                                                           const double* __restrict__ qhat,
-                                                           const uint8_t* __restrict__ sub, int sid,
-                                                           const TF* __restrict__ Fin, int r, int64_t n_out,
-                                                           TF* Xout, int* err) {
-    __shared__ double Gs[LS_WARPS][RMAX][RMAX + 1];
-    __shared__ double bs[LS_WARPS][RMAX];
+__global__ void __launch_bounds__(32 * LS_WARPS) seg_gram_kernel(
+    const int64_t* __restrict__ seg_b, const int64_t* __restrict__ seg_e, int64_t nseg,
+    const int32_t* __restrict__ idx, const int64_t* __restrict__ pos, const TV* __restrict__ vals,
+    const double* __restrict__ qhat, const uint8_t* __restrict__ sub, int sid, const TF* __restrict__ Fin, int r,
+    TG* part) {
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t o = (int64_t)blockIdx.x * LS_WARPS + wid;
-    if (o >= n_out) return;
+    const int64_t s = (int64_t)blockIdx.x * LS_WARPS + wid;
+    if (s >= nseg) return;
     TG g[RMAX];
 #pragma unroll
     for (int a = 0; a < RMAX; ++a) g[a] = TG(0);
     TG bl = TG(0);
-    const int64_t p0 = ptr[o], p1 = ptr[o + 1];
+    const int64_t p0 = seg_b[s], p1 = seg_e[s];
     for (int64_t base = p0; base < p1; base += 32) {
         const int64_t p = base + lane;
         int32_t in = 0;
@@ -184,68 +247,127 @@ __global__ void __launch_bounds__(32 * LS_WARPS) ls_kernel(const int64_t* __rest
             mv = (TG)vals[e];
         }
         const int cnt = (int)(p1 - base < 32 ? p1 - base : 32);
-        for (int s = 0; s < cnt; ++s) {
-            const int32_t in_s = __shfl_sync(0xffffffffu, in, s);
-            const TG w_s = __shfl_sync(0xffffffffu, wv, s);
-            const TG m_s = __shfl_sync(0xffffffffu, mv, s);
-            const TG f = lane < r ? (TG)Fin[(int64_t)in_s * r + lane] : TG(0);
-            const TG wf = w_s * f;
+        for (int t = 0; t < cnt; ++t) {
+            const int32_t in_t = __shfl_sync(0xffffffffu, in, t);
+            const TG w_t = __shfl_sync(0xffffffffu, wv, t);
+            const TG m_t = __shfl_sync(0xffffffffu, mv, t);
+            const TG f = lane < r ? (TG)Fin[(int64_t)in_t * r + lane] : TG(0);
+            const TG wf = w_t * f;
 #pragma unroll
             for (int a = 0; a < RMAX; ++a) g[a] = fma(wf, __shfl_sync(0xffffffffu, f, a), g[a]);
-            bl = fma(wf, m_s, bl);
+            bl = fma(wf, m_t, bl);
         }
     }
-    // G (column lane) -> shared binary64; trace; ridge
+    TG* dst = part + s * (int64_t)(r * r + r);
     if (lane < r) {
 #pragma unroll
         for (int a = 0; a < RMAX; ++a)
-            if (a < r) Gs[wid][a][lane] = (double)g[a];
-        bs[wid][lane] = (double)bl;
+            if (a < r) dst[a * r + lane] = g[a];
+        dst[r * r + lane] = bl;
+    }
+}
+
+// Gc[o] = sum of the segment partials of output row o, in segment order and in binary64: the packed lower triangle
+// of G (r (r + 1) / 2 values) followed by b (r values). One warp per row; lanes over the r^2 + r partial values,
+// so every segment is read with coalesced loads.
+template <typename TG>
+__global__ void __launch_bounds__(256) seg_reduce_kernel(const int64_t* __restrict__ seg_start,
+                                                         const TG* __restrict__ part, int r, int64_t n_out,
+                                                         double* Gc) {
+    const int64_t o = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (o >= n_out) return;
+    const int stride = r * r + r;
+    const int nt = r * (r + 1) / 2;
+    double* dst = Gc + o * (int64_t)(nt + r);
+    for (int e0 = 0; e0 < stride; e0 += 32) {
+        const int e = e0 + lane;
+        double acc = 0.0;
+        if (e < stride)
+            for (int64_t s = seg_start[o]; s < seg_start[o + 1]; ++s) acc += (double)part[s * (int64_t)stride + e];
+        if (e < r * r) {
+            const int i = e / r, j = e - i * r;
+            if (j <= i) dst[i * (i + 1) / 2 + j] = acc;
+        } else if (e < stride) {
+            dst[nt + (e - r * r)] = acc;
+        }
+    }
+}
+
+// One thread per output row (32 rows per CTA): ridge, Cholesky and solve of its compact binary64 system. The 32
+// systems are first staged into shared memory as [element][lane] with coalesced loads, so every later access is
+// conflict-free and nothing spills to local memory.
+template <typename TF, int RMAX>
+__global__ void __launch_bounds__(32) solve_kernel(const double* __restrict__ Gc, int r, int64_t n_out, TF* Xout,
+                                                   int* err) {
+    constexpr int NT = RMAX * (RMAX + 1) / 2;
+    extern __shared__ double solve_sm[];
+    const int lane = threadIdx.x;
+    double* Ls = solve_sm;               // [NT][32]
+    double* ys = solve_sm + NT * 32;     // [RMAX][32]
+    double* ri = ys + RMAX * 32;         // [RMAX][32]
+#define LL(e) Ls[(e) * 32 + lane]
+#define YY(i) ys[(i) * 32 + lane]
+#define RI(i) ri[(i) * 32 + lane]
+    const int nt = r * (r + 1) / 2;
+    const int64_t o0 = (int64_t)blockIdx.x * 32;
+    for (int q = 0; q < 32 && o0 + q < n_out; ++q) {
+        const double* src = Gc + (o0 + q) * (int64_t)(nt + r);
+        for (int e = lane; e < nt + r; e += 32) {
+            if (e < nt) Ls[e * 32 + q] = src[e];
+            else ys[(e - nt) * 32 + q] = src[e];
+        }
     }
     __syncwarp();
+    const int64_t o = o0 + lane;
+    if (o >= n_out) return;
     double tr = 0.0;
-    for (int a = 0; a < r; ++a) tr += Gs[wid][a][a];
+    for (int i = 0; i < r; ++i) tr += LL(i * (i + 1) / 2 + i);
     if (!(tr > 0.0)) {
-        if (lane < r) Xout[o * r + lane] = TF(0);
+        for (int i = 0; i < r; ++i) Xout[o * r + i] = TF(0);
         return;
     }
-    if (lane < r) Gs[wid][lane][lane] += 1e-10 * tr / (double)r;
-    __syncwarp();
-    // in-place lower Cholesky
+    const double lam = 1e-10 * tr / (double)r;
+    for (int i = 0; i < r; ++i) LL(i * (i + 1) / 2 + i) += lam;
     for (int j = 0; j < r; ++j) {
-        const double d = Gs[wid][j][j];
+        const int jb = j * (j + 1) / 2;
+        double d = LL(jb + j);
+        for (int k = 0; k < j; ++k) d -= LL(jb + k) * LL(jb + k);
         if (!(d > 0.0)) {
-            if (lane == 0) set_error(err, DEVERR_NUMERIC);
-            if (lane < r) Xout[o * r + lane] = TF(0);
+            set_error(err, DEVERR_NUMERIC);
+            for (int i = 0; i < r; ++i) Xout[o * r + i] = TF(0);
             return;
         }
-        const double sd = sqrt(d);
-        __syncwarp();
-        if (lane == j) Gs[wid][j][j] = sd;
-        if (lane > j && lane < r) Gs[wid][lane][j] /= sd;
-        __syncwarp();
-        if (lane > j && lane < r) {
-            const double lij = Gs[wid][lane][j];
-            for (int kk = j + 1; kk <= lane; ++kk) Gs[wid][lane][kk] -= lij * Gs[wid][kk][j];
+        const double rj = rsqrt_refined(d);
+        RI(j) = rj;
+        LL(jb + j) = d * rj;
+        for (int i = j + 1; i < r; ++i) {
+            const int ib = i * (i + 1) / 2;
+            double v = LL(ib + j);
+            for (int k = 0; k < j; ++k) v -= LL(ib + k) * LL(jb + k);
+            LL(ib + j) = v * rj;
         }
-        __syncwarp();
     }
-    // forward L y = b, then backward L^T x = y (lane j finalises entry j, the others update)
-    for (int j = 0; j < r; ++j) {
-        if (lane == j) bs[wid][j] /= Gs[wid][j][j];
-        __syncwarp();
-        const double yj = bs[wid][j];
-        if (lane > j && lane < r) bs[wid][lane] -= Gs[wid][lane][j] * yj;
-        __syncwarp();
+    for (int i = 0; i < r; ++i) {   // L z = y
+        const int ib = i * (i + 1) / 2;
+        double v = YY(i);
+        for (int k = 0; k < i; ++k) v -= LL(ib + k) * YY(k);
+        YY(i) = v * RI(i);
     }
-    for (int j = r - 1; j >= 0; --j) {
-        if (lane == j) bs[wid][j] /= Gs[wid][j][j];
-        __syncwarp();
-        const double xj = bs[wid][j];
-        if (lane < j) bs[wid][lane] -= Gs[wid][j][lane] * xj;
-        __syncwarp();
+    for (int i = r - 1; i >= 0; --i) {   // L^T x = z
+        double v = YY(i);
+        for (int k = i + 1; k < r; ++k) v -= LL(k * (k + 1) / 2 + i) * YY(k);
+        YY(i) = v * RI(i);
     }
-    if (lane < r) Xout[o * r + lane] = (TF)bs[wid][lane];
+    for (int i = 0; i < r; ++i) Xout[o * r + i] = (TF)YY(i);
+#undef LL
+#undef YY
+#undef RI
+}
+
+template <int RMAX>
+constexpr int solve_smem_bytes() {
+    return (RMAX * (RMAX + 1) / 2 + 2 * RMAX) * 32 * 8;
 }
 
 // ---------------------------------------------------------------------------------------------------------------
@@ -268,8 +390,8 @@ __global__ void core_kernel(const double* __restrict__ Ru, const double* __restr
     H[e] = v;
 }
 
-// From the eigenvectors of H (2r x 2r, sorted decreasing): S[c] = lambda_c, W = sqrt2 * top block, Z = sqrt2 *
-// bottom block of the first r eigenvectors, each renormalised (a zero singular value leaves a zero column).
+// From the eigenvectors of H (2r x 2r, sorted decreasing): S[c] = lambda_c, W = top block, Z = bottom block of the
+// first r eigenvectors, each renormalised (a zero singular value leaves a zero column).
 __global__ void core_split_kernel(const double* __restrict__ ev, const double* __restrict__ EV, int r, double* S,
                                   double* Wc, double* Zc) {
     const int c = threadIdx.x;
@@ -280,13 +402,13 @@ __global__ void core_split_kernel(const double* __restrict__ ev, const double* _
         nu += EV[i * n + c] * EV[i * n + c];
         nv += EV[(r + i) * n + c] * EV[(r + i) * n + c];
     }
-    nu = sqrt(nu);
-    nv = sqrt(nv);
     const double lam = ev[c];
+    const double iu = (lam > 0.0 && nu > 0.0) ? rsqrt_refined(nu) : 0.0;
+    const double iv = (lam > 0.0 && nv > 0.0) ? rsqrt_refined(nv) : 0.0;
     S[c] = lam > 0.0 ? lam : 0.0;
     for (int i = 0; i < r; ++i) {
-        Wc[i * r + c] = (lam > 0.0 && nu > 0.0) ? EV[i * n + c] / nu : 0.0;
-        Zc[i * r + c] = (lam > 0.0 && nv > 0.0) ? EV[(r + i) * n + c] / nv : 0.0;
+        Wc[i * r + c] = EV[i * n + c] * iu;
+        Zc[i * r + c] = EV[(r + i) * n + c] * iv;
     }
 }
 
@@ -337,6 +459,15 @@ __global__ void sign_kernel(double* U, int64_t n1, double* V, int64_t n2, int r)
     for (int64_t i = threadIdx.x; i < n2; i += blockDim.x) V[i * r + c] = -V[i * r + c];
 }
 
+__global__ void upper_mul_kernel(const double* __restrict__ R2, const double* __restrict__ R1, int b, double* R) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= b * b) return;
+    const int i = e / b, j = e - i * b;
+    double s = 0.0;
+    for (int l = i; l <= j; ++l) s += R2[i * b + l] * R1[l * b + j];
+    R[e] = j >= i ? s : 0.0;
+}
+
 // ---------------------------------------------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------------------------------------------
@@ -352,56 +483,76 @@ struct Arena {
     }
 };
 
-unsigned nblocks(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+unsigned nblocks(int64_t n, int threads) { return (unsigned)std::max<int64_t>(1, (n + threads - 1) / threads); }
 
 // Gram of X (n x a) with Y (n x b) into G (a x b), fixed-order reduction.
 template <typename TX, typename TY>
 void gram(const TX* X, const TY* Y, int64_t n, int a, int b, double* part, double* G, cudaStream_t st) {
     const int nblk = (int)std::max<int64_t>(1, (n + GRAM_ROWS_PER_BLOCK - 1) / GRAM_ROWS_PER_BLOCK);
     gram_partial_kernel<TX, TY><<<smp::counted(nblk), 256, 0, st>>>(X, Y, n, a, b, part);
-    gram_reduce_kernel<<<smp::counted(nblocks(a * b, 256)), 256, 0, st>>>(part, nblk, a * b, G);
+    gram_reduce_kernel<<<smp::counted(nblocks(a * b * 32, 256)), 256, 0, st>>>(part, nblk, a * b, G);
 }
 
-// Cholesky-QR twice: Q = X R^-1 with X = Q R; Rout = R2 R1 (upper). Q may alias nothing of X.
-template <typename TX, typename TQ>
-void cholqr2(const TX* X, int64_t n, int b, TQ* Q, double* part, double* G, double* R1, double* R2, double* Rout,
-             cudaStream_t st);
-
-__global__ void upper_mul_kernel(const double* __restrict__ R2, const double* __restrict__ R1, int b, double* R) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= b * b) return;
-    const int i = e / b, j = e - i * b;
-    double s = 0.0;
-    for (int l = i; l <= j; ++l) s += R2[i * b + l] * R1[l * b + j];
-    R[e] = j >= i ? s : 0.0;
-}
-
-template <typename TX, typename TQ>
+// Cholesky-QR twice: Q = X R^-1 with X = Q R; Rout = R2 R1 (upper). Q may alias X. The Gram matrices and the
+// factorisations are binary64; the substitutions run in TC.
+template <typename TX, typename TQ, typename TC>
 void cholqr2(const TX* X, int64_t n, int b, TQ* Q, double* part, double* G, double* R1, double* R2, double* Rout,
              cudaStream_t st) {
     gram<TX, TX>(X, X, n, b, b, part, G, st);
-    chol_kernel<<<smp::counted(1), 32, 0, st>>>(G, b, R1, 1e-28, nullptr);
-    apply_rinv_kernel<TX, TQ><<<smp::counted(nblocks(n, 128)), 128, 0, st>>>(X, n, b, R1, Q);
+    chol_kernel<<<smp::counted(1), 32, 0, st>>>(G, b, R1, 1e-28);
+    apply_rinv_kernel<TX, TQ, TC><<<smp::counted(nblocks(n, 128)), 128, 0, st>>>(X, n, b, R1, Q);
     gram<TQ, TQ>(Q, Q, n, b, b, part, G, st);
-    chol_kernel<<<smp::counted(1), 32, 0, st>>>(G, b, R2, 1e-28, nullptr);
-    apply_rinv_kernel<TQ, TQ><<<smp::counted(nblocks(n, 128)), 128, 0, st>>>(Q, n, b, R2, Q);
+    chol_kernel<<<smp::counted(1), 32, 0, st>>>(G, b, R2, 1e-28);
+    apply_rinv_kernel<TQ, TQ, TC><<<smp::counted(nblocks(n, 128)), 128, 0, st>>>(Q, n, b, R2, Q);
     if (Rout) upper_mul_kernel<<<smp::counted(nblocks(b * b, 256)), 256, 0, st>>>(R2, R1, b, Rout);
 }
 
+struct Segments {
+    int64_t* start = nullptr;   // [n_out + 1]
+    int64_t* b = nullptr;       // [nseg]
+    int64_t* e = nullptr;       // [nseg]
+    int64_t nseg = 0;
+};
+
+// Y (n_out x b) = sum over each output row's entries of val * X[idx]; Yp: scratch of nseg x b partials.
+template <typename TY>
+void spmm(const Segments& sg, const int32_t* idx, const TY* val, const TY* X, int64_t n_out, int b, TY* Yp, TY* Y,
+          cudaStream_t st) {
+    const unsigned g = nblocks(sg.nseg * 32, 256);
+    if (b <= 32) spmm_seg_kernel<TY, 1><<<smp::counted(g), 256, 0, st>>>(sg.b, sg.e, sg.nseg, idx, val, X, b, Yp);
+    else if (b <= 64) spmm_seg_kernel<TY, 2><<<smp::counted(g), 256, 0, st>>>(sg.b, sg.e, sg.nseg, idx, val, X, b, Yp);
+    else spmm_seg_kernel<TY, 3><<<smp::counted(g), 256, 0, st>>>(sg.b, sg.e, sg.nseg, idx, val, X, b, Yp);
+    spmm_reduce_kernel<TY><<<smp::counted(nblocks(n_out * b, 256)), 256, 0, st>>>(sg.start, Yp, n_out, b, Y);
+}
+
 template <typename TF, typename TG, typename TV>
-void launch_ls(int r, const int64_t* ptr, const int32_t* idx, const int64_t* pos, const TV* vals,
-               const double* qhat, const uint8_t* sub, int sid, const TF* Fin, int64_t n_out, TF* Xout, int* err,
-               cudaStream_t st) {
-    const unsigned g = nblocks(n_out, LS_WARPS);
-    if (r <= 8)
-        ls_kernel<TF, TG, TV, 8><<<smp::counted(g), 32 * LS_WARPS, 0, st>>>(ptr, idx, pos, vals, qhat, sub, sid, Fin, r, n_out,
-                                                              Xout, err);
-    else if (r <= 16)
-        ls_kernel<TF, TG, TV, 16><<<smp::counted(g), 32 * LS_WARPS, 0, st>>>(ptr, idx, pos, vals, qhat, sub, sid, Fin, r,
-                                                               n_out, Xout, err);
-    else
-        ls_kernel<TF, TG, TV, 32><<<smp::counted(g), 32 * LS_WARPS, 0, st>>>(ptr, idx, pos, vals, qhat, sub, sid, Fin, r,
-                                                               n_out, Xout, err);
+void launch_ls(int r, const Segments& sg, const int32_t* idx, const int64_t* pos, const TV* vals,
+               const double* qhat, const uint8_t* sub, int sid, const TF* Fin, int64_t n_out, TG* part, double* Gc,
+               TF* Xout, int* err, cudaStream_t st) {
+    const unsigned g = nblocks(sg.nseg, LS_WARPS);
+    const unsigned gr = nblocks(n_out * 32, 256);
+    const unsigned gs = nblocks(n_out, 32);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(solve_kernel<TF, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, solve_smem_bytes<32>());
+        attr = true;
+    }
+    if (r <= 8) {
+        seg_gram_kernel<TF, TG, TV, 8><<<smp::counted(g), 32 * LS_WARPS, 0, st>>>(sg.b, sg.e, sg.nseg, idx, pos,
+                                                                                  vals, qhat, sub, sid, Fin, r, part);
+        seg_reduce_kernel<TG><<<smp::counted(gr), 256, 0, st>>>(sg.start, part, r, n_out, Gc);
+        solve_kernel<TF, 8><<<smp::counted(gs), 32, solve_smem_bytes<8>(), st>>>(Gc, r, n_out, Xout, err);
+    } else if (r <= 16) {
+        seg_gram_kernel<TF, TG, TV, 16><<<smp::counted(g), 32 * LS_WARPS, 0, st>>>(sg.b, sg.e, sg.nseg, idx, pos,
+                                                                                   vals, qhat, sub, sid, Fin, r, part);
+        seg_reduce_kernel<TG><<<smp::counted(gr), 256, 0, st>>>(sg.start, part, r, n_out, Gc);
+        solve_kernel<TF, 16><<<smp::counted(gs), 32, solve_smem_bytes<16>(), st>>>(Gc, r, n_out, Xout, err);
+    } else {
+        seg_gram_kernel<TF, TG, TV, 32><<<smp::counted(g), 32 * LS_WARPS, 0, st>>>(sg.b, sg.e, sg.nseg, idx, pos,
+                                                                                   vals, qhat, sub, sid, Fin, r, part);
+        seg_reduce_kernel<TG><<<smp::counted(gr), 256, 0, st>>>(sg.start, part, r, n_out, Gc);
+        solve_kernel<TF, 32><<<smp::counted(gs), 32, solve_smem_bytes<32>(), st>>>(Gc, r, n_out, Xout, err);
+    }
 }
 
 template <typename TV, typename TF, typename TG, typename TY>
@@ -413,35 +564,41 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
     const bool split = (flags & SMP_SPLIT_OMEGA) != 0;
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
 
-    // scratch sizes
+    // segments of the CSR rows and the CSC columns: an upper bound on their count sizes the scratch
+    const int64_t nseg_max = nnz / SEG + n1 + n2 + 2;
     const int64_t nmax = std::max(n1, n2);
     const int64_t gblk = std::max<int64_t>(1, (nmax + GRAM_ROWS_PER_BLOCK - 1) / GRAM_ROWS_PER_BLOCK);
     size_t need = 0;
     auto add = [&](int64_t n, size_t sz) { need += ((size_t)std::max<int64_t>(n, 1) * sz + 511) & ~size_t(255); };
-    add(nnz, 4);                 // erow
-    add(nnz, 1);                 // sub
-    add(nnz, sizeof(TY));        // rv
-    add(n1 * b, sizeof(TY));     // Y
-    add(n2 * b, sizeof(TY));     // Z
-    add(n1 * b, sizeof(TY));     // Ytmp
-    add(gblk * b * b, 8);        // gram partials
-    add(5 * b * b + 4 * b, 8);   // G, R1, R2, E, evals...
-    add(2 * n1 * r, 8);          // U0, U0prev
-    add(n1 * r, sizeof(TF));     // Uf
-    add(n2 * r, sizeof(TF));     // Vf
-    add(n1 * r, 8);              // Qu
-    add(n2 * r, 8);              // Qv
-    add(8 * r * r + 8 * r, 8);   // Ru, Rv, H, EV, W, Z, ...
+    add(nnz, 1);                             // sub
+    add(2 * nnz, sizeof(TY));                // rv, rv_csc
+    add(n1 * b, sizeof(TY));                 // Y
+    add(n2 * b, sizeof(TY));                 // Z
+    add(n1 * b, sizeof(TY));                 // Ytmp
+    add(gblk * MAX_SMALL * MAX_SMALL, 8);    // gram partials
+    add(5 * b * b + 4 * b, 8);               // G, R1, R2, E, evals
+    add(2 * n1 * r, 8);                      // U0, U0prev
+    add(n1 * r, sizeof(TF));                 // Uf
+    add(n2 * r, sizeof(TF));                 // Vf
+    add(n1 * r, 8);                          // Qu
+    add(n2 * r, 8);                          // Qv
+    add(12 * r * r + 8 * r, 8);              // Ru, Rv, H, EV, W, Z, ...
+    add(n1 + n2 + 2, 4);                     // segment counts
+    add(n1 + n2 + 4, 8);                     // segment starts
+    add(4 * nseg_max, 8);                    // segment begins / ends
+    add(nseg_max * (int64_t)(r * r + r), sizeof(TG));   // LS partials
+    add(nseg_max * (int64_t)b, sizeof(TY));             // SpMM segment partials
+    add(nmax * (int64_t)(r * (r + 1) / 2 + r), 8);      // compact per-row systems
     void* ws = nullptr;
     if (cudaMallocAsync(&ws, need, st) != cudaSuccess) return fail(c, SMP_ENOMEM, "smp_waltmin: scratch");
     Arena ar{(char*)ws, 0, need};
-    int32_t* erow = ar.take<int32_t>(nnz);
     uint8_t* sub = ar.take<uint8_t>(nnz);
     TY* rv = ar.take<TY>(nnz);
+    TY* rv_csc = ar.take<TY>(nnz);
     TY* Y = ar.take<TY>(n1 * b);
     TY* Z = ar.take<TY>(n2 * b);
     TY* Yt = ar.take<TY>(n1 * b);
-    double* part = ar.take<double>(gblk * b * b);
+    double* part = ar.take<double>(gblk * MAX_SMALL * MAX_SMALL);
     double* G = ar.take<double>(b * b);
     double* R1 = ar.take<double>(b * b);
     double* R2 = ar.take<double>(b * b);
@@ -463,83 +620,142 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
     double* Rx1 = ar.take<double>(r * r);
     double* Rx2 = ar.take<double>(r * r);
     double* Gx = ar.take<double>(r * r);
+    int32_t* seg_cnt = ar.take<int32_t>(n1 + n2 + 2);
+    Segments rows_sg, cols_sg;
+    rows_sg.start = ar.take<int64_t>(n1 + 1);
+    cols_sg.start = ar.take<int64_t>(n2 + 1);
+    int64_t* seg_be = ar.take<int64_t>(4 * nseg_max);
+    TG* lspart = ar.take<TG>(nseg_max * (int64_t)(r * r + r));
+    TY* Yp = ar.take<TY>(nseg_max * (int64_t)b);
+    double* Gc = ar.take<double>(nmax * (int64_t)(r * (r + 1) / 2 + r));
 
     static bool attr_done = false;
     if (!attr_done) {
-        cudaFuncSetAttribute(jacobi_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(jacobi_eig_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              2 * MAX_SMALL * (MAX_SMALL + 1) * 8);
+        cudaFuncSetAttribute(jacobi_eig_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             2 * MAX_SMALL * (MAX_SMALL + 1) * 4);
         attr_done = true;
     }
-    auto jacobi = [&](const double* Ain, int n, double tol, double* evals, double* Vout) {
-        jacobi_eig_kernel<<<smp::counted(1), 256, 2 * n * (n + 1) * 8, st>>>(Ain, n, tol, 40, evals, Vout);
-    };
 
-    if (nnz > 0) erow_kernel<<<smp::counted(nblocks(n1 * 32, 256)), 256, 0, st>>>(c->row_ptr, n1, erow);
+    // segments (Omega is fixed for the whole call); the count copy is the call's only early host sync
+    seg_count_kernel<<<smp::counted(nblocks(n1, 256)), 256, 0, st>>>(c->row_ptr, n1, seg_cnt);
+    scan_kernel<<<smp::counted(1), 1024, 0, st>>>(seg_cnt, n1, rows_sg.start);
+    seg_count_kernel<<<smp::counted(nblocks(n2, 256)), 256, 0, st>>>(c->col_ptr, n2, seg_cnt + n1 + 1);
+    scan_kernel<<<smp::counted(1), 1024, 0, st>>>(seg_cnt + n1 + 1, n2, cols_sg.start);
+    int64_t counts[2] = {0, 0};
+    cudaMemcpyAsync(&counts[0], rows_sg.start + n1, 8, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&counts[1], cols_sg.start + n2, 8, cudaMemcpyDeviceToHost, st);
+    cudaError_t ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) {
+        cudaFreeAsync(ws, st);
+        return check_cuda(c, ce, "smp_waltmin: segment counts");
+    }
+    rows_sg.nseg = counts[0];
+    cols_sg.nseg = counts[1];
+    rows_sg.b = seg_be;
+    rows_sg.e = seg_be + rows_sg.nseg;
+    cols_sg.b = seg_be + 2 * rows_sg.nseg;
+    cols_sg.e = cols_sg.b + cols_sg.nseg;
+    seg_fill_kernel<<<smp::counted(nblocks(n1, 256)), 256, 0, st>>>(c->row_ptr, rows_sg.start, n1, rows_sg.b,
+                                                                    rows_sg.e);
+    seg_fill_kernel<<<smp::counted(nblocks(n2, 256)), 256, 0, st>>>(c->col_ptr, cols_sg.start, n2, cols_sg.b,
+                                                                    cols_sg.e);
+
     if (split && nnz > 0)
-        split_kernel<<<smp::counted(nblocks(nnz, 256)), 256, 0, st>>>(erow, c->col, nnz, T, k0, k1, sub);
+        split_kernel<<<smp::counted(nblocks(nnz, 256)), 256, 0, st>>>(c->erow, c->col, nnz, T, k0, k1, sub);
     const uint8_t* subp = split ? sub : nullptr;
-
+    auto jacobi64 = [&](const double* Ain, int n, double tol, double* evals, double* Vout) {
+        jacobi_eig_kernel<double><<<smp::counted(1), 256, 2 * n * (n + 1) * 8, st>>>(Ain, n, tol, 40, evals, Vout);
+    };
     smp_status status = SMP_OK;
     if (flags & SMP_INIT_GIVEN) {
         convert_kernel<double, TF><<<smp::counted(nblocks(n1 * r, 256)), 256, 0, st>>>(U_init, n1 * r, Uf);
     } else {
-        // R_Omega0(M~) values
-        if (nnz > 0) rvals_kernel<TV, TY><<<smp::counted(nblocks(nnz, 256)), 256, 0, st>>>(vals, c->qhat, subp, 0, nnz, rv);
+        // R_Omega0(M~) values in CSR and CSC order
+        if (nnz > 0)
+            rvals_kernel<TV, TY><<<smp::counted(nblocks(nnz, 256)), 256, 0, st>>>(vals, c->qhat, subp, 0,
+                                                                                  c->csc_pos, nnz, rv, rv_csc);
         start_block_kernel<TY><<<smp::counted(nblocks(n1 * ((b + 3) / 4), 256)), 256, 0, st>>>(n1, b, k0, k1, Y);
-        cholqr2<TY, TY>(Y, n1, b, Y, part, G, R1, R2, nullptr, st);
+        cholqr2<TY, TY, TY>(Y, n1, b, Y, part, G, R1, R2, nullptr, st);
+        // Convergence. binary32 iterates: the top-r Ritz values (binary32 Jacobi) change by < 1e-6 relative between
+        // checks. binary64 iterates: the top-r Ritz subspace (binary64 Jacobi) moves by < 1e-11 between checks.
         const bool dbl = sizeof(TY) == 8;
-        const int max_iter = dbl ? 400 : 300;
-        const double tol = dbl ? 1e-11 : 1e-5;
-        const int check = 10;
-        std::vector<double> hbuf(2);
+        const int max_iter = dbl ? 400 : 200;
+        const int every = dbl ? 4 : 2;
+        bool have_prev = false;
+        std::vector<double> prev_ev(b, 0.0), cur_ev(b, 0.0);
         for (int it = 1; it <= max_iter; ++it) {
-            spmm_csc_kernel<TY><<<smp::counted(nblocks(n2 * 32, 256)), 256, 0, st>>>(c->col_ptr, c->csc_row, c->csc_pos, rv, Y,
-                                                                      n2, b, Z);
-            spmm_csr_kernel<TY><<<smp::counted(nblocks(n1 * 32, 256)), 256, 0, st>>>(c->row_ptr, c->col, rv, Z, n1, b, Yt);
-            cholqr2<TY, TY>(Yt, n1, b, Y, part, G, R1, R2, nullptr, st);
-            if (it % check == 0 || it == max_iter) {
-                // Rayleigh-Ritz on span(Y): C = Z^T Z with Z = R^T Y; U0 = Y E[:, :r]
-                spmm_csc_kernel<TY><<<smp::counted(nblocks(n2 * 32, 256)), 256, 0, st>>>(c->col_ptr, c->csc_row, c->csc_pos,
-                                                                          rv, Y, n2, b, Z);
-                gram<TY, TY>(Z, Z, n2, b, b, part, G, st);
-                jacobi(G, b, 1e-15, ev, E);
+            spmm<TY>(cols_sg, c->csc_row, rv_csc, Y, n2, b, Yp, Z, st);   // Z = R^T Y
+            spmm<TY>(rows_sg, c->col, rv, Z, n1, b, Yp, Yt, st);          // Y = R Z
+            cholqr2<TY, TY, TY>(Yt, n1, b, Y, part, G, R1, R2, nullptr, st);
+            if (it % every != 0 && it != max_iter) continue;
+            spmm<TY>(cols_sg, c->csc_row, rv_csc, Y, n2, b, Yp, Z, st);   // C = Z^T Z, Z = R^T Y
+            gram<TY, TY>(Z, Z, n2, b, b, part, G, st);
+            bool done = false;
+            if (dbl) {
+                jacobi_eig_kernel<double><<<smp::counted(1), 256, 2 * b * (b + 1) * 8, st>>>(G, b, 1e-15, 40, ev, E);
                 ritz_kernel<TY><<<smp::counted(nblocks(n1 * r, 256)), 256, 0, st>>>(Y, E, n1, b, r, U0);
-                if (it > check) {
-                    // subspace change: dist^2 = r - ||U0^T U0prev||_F^2
+                if (have_prev) {
                     gram<double, double>(U0, U0p, n1, r, r, part, Gx, st);
                     std::vector<double> hx(r * r);
-                    if (cudaMemcpyAsync(hx.data(), Gx, sizeof(double) * r * r, cudaMemcpyDeviceToHost, st) !=
-                            cudaSuccess ||
-                        cudaStreamSynchronize(st) != cudaSuccess) {
-                        status = check_cuda(c, cudaGetLastError(), "smp_waltmin init check");
+                    cudaError_t e1 =
+                        cudaMemcpyAsync(hx.data(), Gx, sizeof(double) * r * r, cudaMemcpyDeviceToHost, st);
+                    if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(st);
+                    if (e1 != cudaSuccess) {
+                        status = check_cuda(c, e1, "smp_waltmin init check");
                         break;
                     }
                     double fro = 0.0;
                     for (double v : hx) fro += v * v;
-                    const double d2 = std::max(0.0, (double)r - fro);
-                    if (std::sqrt(d2) < tol) break;
+                    done = std::sqrt(std::max(0.0, (double)r - fro)) < 1e-11;
                 }
                 cudaMemcpyAsync(U0p, U0, sizeof(double) * n1 * r, cudaMemcpyDeviceToDevice, st);
+            } else {
+                jacobi_eig_kernel<float><<<smp::counted(1), 256, 2 * b * (b + 1) * 4, st>>>(G, b, 1e-7, 30, ev, E);
+                cudaError_t e1 = cudaMemcpyAsync(cur_ev.data(), ev, sizeof(double) * b, cudaMemcpyDeviceToHost, st);
+                if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(st);
+                if (e1 != cudaSuccess) {
+                    status = check_cuda(c, e1, "smp_waltmin init check");
+                    break;
+                }
+                if (have_prev) {
+                    double worst = 0.0;
+                    for (int i = 0; i < r; ++i)
+                        worst = std::max(worst, std::fabs(cur_ev[i] - prev_ev[i]) / std::max(cur_ev[0], 1e-300));
+                    done = worst < 1e-6;
+                }
+                prev_ev = cur_ev;
+            }
+            have_prev = true;
+            if (done || it == max_iter) {
+                if (!dbl) {   // final Rayleigh-Ritz vectors in binary64
+                    jacobi_eig_kernel<double><<<smp::counted(1), 256, 2 * b * (b + 1) * 8, st>>>(G, b, 1e-15, 40, ev,
+                                                                                                E);
+                    ritz_kernel<TY><<<smp::counted(nblocks(n1 * r, 256)), 256, 0, st>>>(Y, E, n1, b, r, U0);
+                }
+                break;
             }
         }
         if (status == SMP_OK) {
-            if (!(flags & SMP_NO_TRIM)) trim_kernel<<<smp::counted(nblocks(n1, 256)), 256, 0, st>>>(U0, n1, r, c->s_all, c->F);
+            if (!(flags & SMP_NO_TRIM))
+                trim_kernel<<<smp::counted(nblocks(n1, 256)), 256, 0, st>>>(U0, n1, r, c->s_all, c->F);
             convert_kernel<double, TF><<<smp::counted(nblocks(n1 * r, 256)), 256, 0, st>>>(U0, n1 * r, Uf);
         }
     }
     if (status == SMP_OK) {
         for (int t = 0; t < T; ++t) {
-            launch_ls<TF, TG, TV>(r, c->col_ptr, c->csc_row, c->csc_pos, vals, c->qhat, subp, 2 * t + 1, Uf, n2, Vf,
-                                  c->dev_err, st);
-            launch_ls<TF, TG, TV>(r, c->row_ptr, c->col, nullptr, vals, c->qhat, subp, 2 * t + 2, Vf, n1, Uf,
-                                  c->dev_err, st);
+            launch_ls<TF, TG, TV>(r, cols_sg, c->csc_row, c->csc_pos, vals, c->qhat, subp, 2 * t + 1, Uf, n2, lspart,
+                                  Gc, Vf, c->dev_err, st);
+            launch_ls<TF, TG, TV>(r, rows_sg, c->col, nullptr, vals, c->qhat, subp, 2 * t + 2, Vf, n1, lspart, Gc,
+                                  Uf, c->dev_err, st);
         }
         if (T == 0) cudaMemsetAsync(Vf, 0, sizeof(TF) * n2 * r, st);
         // canonical form
-        cholqr2<TF, double>(Uf, n1, r, Qu, part, Gx, Rx1, Rx2, Ru, st);
-        cholqr2<TF, double>(Vf, n2, r, Qv, part, Gx, Rx1, Rx2, Rv, st);
+        cholqr2<TF, double, double>(Uf, n1, r, Qu, part, Gx, Rx1, Rx2, Ru, st);
+        cholqr2<TF, double, double>(Vf, n2, r, Qv, part, Gx, Rx1, Rx2, Rv, st);
         core_kernel<<<smp::counted(nblocks(4 * r * r, 256)), 256, 0, st>>>(Ru, Rv, r, H);
-        jacobi(H, 2 * r, 1e-16, evh, EV);
+        jacobi64(H, 2 * r, 1e-16, evh, EV);
         core_split_kernel<<<smp::counted(1), 32, 0, st>>>(evh, EV, r, S, Wc, Zc);
         small_right_mul_kernel<<<smp::counted(nblocks(n1 * r, 256)), 256, 0, st>>>(Qu, Wc, n1, r, U);
         small_right_mul_kernel<<<smp::counted(nblocks(n2 * r, 256)), 256, 0, st>>>(Qv, Zc, n2, r, V);
