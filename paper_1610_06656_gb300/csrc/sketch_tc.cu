@@ -8,8 +8,9 @@
 //     (sketch row, data row); regenerating it inside each column tile would cost (n1 + n2) / 128 times more.
 //  2. sketch_tc_kernel: one CTA per (128-column tile, row split). Warp 0 issues TMA loads of the data tile (rows
 //     of A are contiguous along the columns, so the tile lands column-major for the MMA: 32-column x 8-row
-//     boxes, 128-byte swizzle) and of the Pi tile (K-major, 64-byte swizzle, 256-row boxes) into a 4-stage
-//     shared-memory ring guarded by mbarriers. kind::tf32 takes K-major operands only, so warps 4-7 (one
+//     boxes, 128-byte swizzle) into an 8-slot staging ring; warp 2 issues TMA loads of the Pi tile (K-major,
+//     64-byte swizzle, 256-row boxes) into a 4-slot ring, all guarded by mbarriers (the deeper data ring keeps
+//     more HBM reads in flight). kind::tf32 takes K-major operands only, so warps 4-7 (one
 //     32-column box each) read every staged element once, fold x^2 into compensated (TwoSum + FMA residual)
 //     column sums, round x to TF32 (cvt.rna) and write it back K-major (64-byte swizzle, conflict-free 16-byte
 //     stores). Warp 1 (one thread) issues tcgen05.mma kind::tf32 with M = 128 data columns and N = 256 sketch
@@ -31,7 +32,8 @@ namespace {
 
 constexpr int TILE_M = 128;        // data columns per CTA (MMA M)
 constexpr int KS = 16;             // data rows per pipeline stage (two K = 8 MMA slices)
-constexpr int STAGES = 4;
+constexpr int STAGES = 4;          // ring of (K-major data copy, Pi tile) consumed by the MMA
+constexpr int DSTAGES = 8;         // deeper ring of staged data tiles (TMA target), freed by the copy warps
 constexpr int PI_BOX_ROWS = 256;   // sketch rows per Pi box (MMA N)
 constexpr int MAX_KC = 512;        // sketch rows per CTA (TMEM columns)
 constexpr int DATA_BOX_ROWS = 8;
@@ -41,11 +43,28 @@ constexpr int KGROUP_BYTES = 4 * DATA_BOX_BYTES;            // one 8-row group o
 constexpr int A_STAGE_BYTES = TILE_M * KS * 4;             // K-major copy: 128 rows x 64 B (64-byte swizzle)
 constexpr int PI_BOX_BYTES = PI_BOX_ROWS * KS * 4;          // 256 rows x KS fp32
 constexpr int PI_STAGE_BYTES = 2 * PI_BOX_BYTES;
-constexpr int A_OFF = DATA_STAGE_BYTES;                     // offsets inside a stage
-constexpr int PI_OFF = DATA_STAGE_BYTES + A_STAGE_BYTES;
-constexpr int STAGE_BYTES = DATA_STAGE_BYTES + A_STAGE_BYTES + PI_STAGE_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
-constexpr int THREADS = 256;
+constexpr int A_OFF = 0;                                    // offsets inside a main-ring stage
+constexpr int PI_OFF = A_STAGE_BYTES;
+constexpr int STAGE_BYTES = A_STAGE_BYTES + PI_STAGE_BYTES;
+constexpr int DRING_BYTES = DSTAGES * DATA_STAGE_BYTES;
+constexpr int SMEM_BYTES = DRING_BYTES + STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+constexpr int THREADS = 512;       // 16 warps: producers 0 and 2, MMA 1, copy warps on schedulers 0, 2, 3
+constexpr int NCOPY = 8;           // copy warps: (32-column box, 8-row group) pairs
+// copy warp c (0..7) is warp COPY_WARP[c]: warp ids 4, 6, 7, 8, 10, 11, 12, 14 live on schedulers 0, 2, 3 (id % 4),
+// leaving scheduler 1 to the MMA issuer (warp 1); tcgen05.mma issue slows down when a busy warp shares it
+__device__ __forceinline__ int copy_index(int warp) {
+    switch (warp) {
+        case 4: return 0;
+        case 6: return 1;
+        case 7: return 2;
+        case 8: return 3;
+        case 10: return 4;
+        case 11: return 5;
+        case 12: return 6;
+        case 14: return 7;
+        default: return -1;
+    }
+}
 constexpr unsigned long long WAIT_NS = 2000000000ull;       // 2 s: far beyond any legitimate wait
 
 // ------------------------------------------------------------------------------------------------ PTX wrappers
@@ -236,26 +255,35 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
     const int64_t cbase = on_b ? args.n1 + col0 : col0;
     const CUtensorMap* tm_data = on_b ? &tm_b : &tm_a;
 
-    // carve shared memory: stages (1024-byte aligned), then barriers
+    // carve shared memory (1024-byte aligned): data ring, main ring, then barriers
     const uint32_t raw = smem_addr(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t* base_ptr = smem_raw + (base - raw);
-    const uint32_t bar_base = base + STAGES * STAGE_BYTES;
-    uint64_t* bars = (uint64_t*)(base_ptr + STAGES * STAGE_BYTES);
-    // bars: [0, S) TMA full, [S, 2S) stage empty, [2S, 3S) K-major copy ready, [3S] accumulator ready; then the
-    // TMEM address word and the abort flag
-    uint32_t* tmem_slot = (uint32_t*)(bars + 3 * STAGES + 1);
+    const uint32_t dring = base;                        // DSTAGES x DATA_STAGE_BYTES
+    const uint32_t mring = base + DRING_BYTES;          // STAGES x STAGE_BYTES
+    const uint32_t bar_base = mring + STAGES * STAGE_BYTES;
+    uint64_t* bars = (uint64_t*)(base_ptr + DRING_BYTES + STAGES * STAGE_BYTES);
+    // bars: [0, D) data full, [D, 2D) data empty, then per main stage: Pi full, copy full, stage empty; then the
+    // accumulator-ready barrier, the TMEM address word and the abort flag
+    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * DSTAGES + 3 * STAGES + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-    auto full_bar = [&](int s) { return bar_base + 8u * s; };
-    auto empty_bar = [&](int s) { return bar_base + 8u * (STAGES + s); };
-    auto afull_bar = [&](int s) { return bar_base + 8u * (2 * STAGES + s); };
-    const uint32_t acc_bar = bar_base + 8u * (3 * STAGES);
+    float hi = 0.f, lo = 0.f;             // copy warps: compensated sum of squares of their column and row group
+    auto dfull_bar = [&](int d) { return bar_base + 8u * d; };
+    auto dempty_bar = [&](int d) { return bar_base + 8u * (DSTAGES + d); };
+    auto pfull_bar = [&](int s) { return bar_base + 8u * (2 * DSTAGES + s); };
+    auto afull_bar = [&](int s) { return bar_base + 8u * (2 * DSTAGES + STAGES + s); };
+    auto empty_bar = [&](int s) { return bar_base + 8u * (2 * DSTAGES + 2 * STAGES + s); };
+    const uint32_t acc_bar = bar_base + 8u * (2 * DSTAGES + 3 * STAGES);
 
     if (threadIdx.x == 0) {
+        for (int d = 0; d < DSTAGES; ++d) {
+            mbar_init(dfull_bar(d), 1);
+            mbar_init(dempty_bar(d), NCOPY);
+        }
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(full_bar(s), 1);
-            mbar_init(empty_bar(s), 1);       // the MMA commit (the copy warps finished before the MMA started)
-            mbar_init(afull_bar(s), 4);       // four copy warps
+            mbar_init(pfull_bar(s), 1);
+            mbar_init(afull_bar(s), NCOPY);
+            mbar_init(empty_bar(s), 1);       // the MMA commit
         }
         mbar_init(acc_bar, 1);
         *abort_flag = 0;
@@ -268,17 +296,13 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
-        // ---------------- TMA producer (the whole warp walks the ring; lane 0 issues)
-        if (lane == 0) {
-            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)tm_data) : "memory");
-            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_pi) : "memory");
-        }
-        const uint32_t bytes = DATA_STAGE_BYTES + args.nh * PI_BOX_BYTES;
+        // ---------------- data producer: column-major data tiles into the staging ring (lane 0 issues)
+        if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)tm_data) : "memory");
         for (int it = 0; it < n_it; ++it) {
-            const int s = it % STAGES;
-            const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+            const int d = it % DSTAGES;
+            const uint32_t ph = (uint32_t)(it / DSTAGES) & 1u;
             bool ok = true;
-            if (it >= STAGES) ok = __all_sync(0xffffffffu, mbar_wait(empty_bar(s), ph ^ 1u, abort_flag));
+            if (it >= DSTAGES) ok = __all_sync(0xffffffffu, mbar_wait(dempty_bar(d), ph ^ 1u, abort_flag));
             if (!ok) {
                 if (lane == 0) {
                     *abort_flag = 1;
@@ -287,17 +311,40 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
                 break;
             }
             if (lane == 0) {
-                mbar_arrive_expect_tx(full_bar(s), bytes);
+                mbar_arrive_expect_tx(dfull_bar(d), DATA_STAGE_BYTES);
                 const int t = (int)(rs + (int64_t)it * KS);
-                const uint32_t dst = base + s * STAGE_BYTES;
+                const uint32_t dst = dring + d * DATA_STAGE_BYTES;
 #pragma unroll
                 for (int g = 0; g < KS / 8; ++g)
 #pragma unroll
                     for (int b = 0; b < 4; ++b)
                         tma_load_2d(dst + g * KGROUP_BYTES + b * DATA_BOX_BYTES, tm_data, (int)col0 + 32 * b,
-                                    t + 8 * g, full_bar(s));
+                                    t + 8 * g, dfull_bar(d));
+            }
+            __syncwarp();
+        }
+    } else if (warp == 2) {
+        // ---------------- Pi producer: Pi tiles into the main ring once the MMA has released the stage
+        if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_pi) : "memory");
+        const uint32_t bytes = args.nh * PI_BOX_BYTES;
+        for (int it = 0; it < n_it; ++it) {
+            const int s = it % STAGES;
+            const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+            bool ok = true;
+            if (it >= STAGES) ok = __all_sync(0xffffffffu, mbar_wait(empty_bar(s), ph ^ 1u, abort_flag));
+            if (!ok) {
+                if (lane == 0) {
+                    *abort_flag = 1;
+                    set_error(args.err, DEVERR_TIMEOUT | (1 << 12));
+                }
+                break;
+            }
+            if (lane == 0) {
+                mbar_arrive_expect_tx(pfull_bar(s), bytes);
+                const int t = (int)(rs + (int64_t)it * KS);
                 for (int h = 0; h < args.nh; ++h)
-                    tma_load_2d(dst + PI_OFF + h * PI_BOX_BYTES, &tm_pi, t, h * PI_BOX_ROWS, full_bar(s));
+                    tma_load_2d(mring + s * STAGE_BYTES + PI_OFF + h * PI_BOX_BYTES, &tm_pi, t, h * PI_BOX_ROWS,
+                                pfull_bar(s));
             }
             __syncwarp();
         }
@@ -309,8 +356,7 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
         for (int it = 0; it < n_it; ++it) {
             const int s = it % STAGES;
             const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-            // Pi arrives by TMA (full), the K-major data copy from the copy warps (afull)
-            ok = __all_sync(0xffffffffu, mbar_wait(full_bar(s), ph, abort_flag) && mbar_wait(afull_bar(s), ph, abort_flag));
+            ok = __all_sync(0xffffffffu, mbar_wait(pfull_bar(s), ph, abort_flag) && mbar_wait(afull_bar(s), ph, abort_flag));
             if (!ok) {
                 if (lane == 0) {
                     *abort_flag = 1;
@@ -320,13 +366,13 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
             }
             tc_fence_after();
             if (lane == 0) {
-                const uint32_t dbase = base + s * STAGE_BYTES;
+                const uint32_t sbase = mring + s * STAGE_BYTES;
 #pragma unroll
                 for (int kb = 0; kb < KS / 8; ++kb) {
                     // both operands K-major, 64B swizzle: rows of 64 B, 8-row groups 512 B apart (SBO), K slice at +32 B
-                    const uint64_t ad = smem_desc(dbase + A_OFF + kb * 32, 16, 512, SWZ_64B);
+                    const uint64_t ad = smem_desc(sbase + A_OFF + kb * 32, 16, 512, SWZ_64B);
                     for (int h = 0; h < args.nh; ++h) {
-                        const uint64_t bd = smem_desc(dbase + PI_OFF + h * PI_BOX_BYTES + kb * 32, 16, 512, SWZ_64B);
+                        const uint64_t bd = smem_desc(sbase + PI_OFF + h * PI_BOX_BYTES + kb * 32, 16, 512, SWZ_64B);
                         mma_tf32(tmem + h * PI_BOX_ROWS, ad, bd, h == args.nh - 1 ? id_last : id_full,
                                  (it > 0 || kb > 0) ? 1u : 0u);
                     }
@@ -337,14 +383,20 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
         }
         if (ok && lane == 0) mma_commit(acc_bar);
         __syncwarp();
-    } else if (warp >= 4) {
-        // ---------------- column sums of squares (one 32-column box per warp), then the TMEM drain
-        const int box = warp - 4;
-        float hi = 0.f, lo = 0.f;
+    } else if (copy_index(warp) >= 0) {
+        // ---------------- copy warps: one (32-column box, 8-row group) each: column sums of squares + K-major TF32
+        // copy of their 8 rows
+        const int ci = copy_index(warp);
+        const int box = ci & 3, grp = ci >> 2;
+        const int m = box * 32 + lane;   // data column within the tile
         for (int it = 0; it < n_it; ++it) {
+            const int d = it % DSTAGES;
+            const uint32_t dph = (uint32_t)(it / DSTAGES) & 1u;
             const int s = it % STAGES;
             const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-            const bool ok = __all_sync(0xffffffffu, mbar_wait(full_bar(s), ph, abort_flag));
+            bool ok = mbar_wait(dfull_bar(d), dph, abort_flag);
+            if (ok && it >= STAGES) ok = mbar_wait(empty_bar(s), ph ^ 1u, abort_flag);   // copy slot free
+            ok = __all_sync(0xffffffffu, ok);
             if (!ok) {
                 if (lane == 0) {
                     *abort_flag = 1;
@@ -352,28 +404,37 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
                 }
                 break;
             }
-            const float* stage_p = (const float*)(base_ptr + s * STAGE_BYTES);
-            // staged tile: 128B swizzle, the 16-byte chunk q of row t of a box sits at chunk q ^ (t & 7)
-            float x[KS];
+            // staged box: 128B swizzle, the 16-byte chunk q of row t sits at chunk q ^ (t & 7)
+            const float* box_p =
+                (const float*)(base_ptr + d * DATA_STAGE_BYTES + grp * KGROUP_BYTES + box * DATA_BOX_BYTES);
+            float x[8];
 #pragma unroll
-            for (int t = 0; t < KS; ++t) {
-                const float* box_p = stage_p + ((t >> 3) * KGROUP_BYTES + box * DATA_BOX_BYTES) / 4;
-                const int tr = t & 7;
-                x[t] = box_p[tr * 32 + (((lane >> 2) ^ tr) << 2) + (lane & 3)];
-                two_sum_square<float>(x[t], hi, lo);
-            }
+            for (int t = 0; t < 8; ++t) x[t] = box_p[t * 32 + (((lane >> 2) ^ t) << 2) + (lane & 3)];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(dempty_bar(d));   // staging read: the producer may refill it
+#pragma unroll
+            for (int t = 0; t < 8; ++t) two_sum_square<float>(x[t], hi, lo);
             // K-major copy: data column m is row m (64 B = KS values); 64B swizzle puts chunk q at q ^ ((m >> 1) & 3)
-            const int m = box * 32 + lane;
-            float4* arow = (float4*)(base_ptr + s * STAGE_BYTES + A_OFF + m * (KS * 4));
-#pragma unroll
-            for (int q = 0; q < KS / 4; ++q)
-                arow[q ^ ((m >> 1) & 3)] =
-                    make_float4(to_tf32(x[4 * q]), to_tf32(x[4 * q + 1]), to_tf32(x[4 * q + 2]), to_tf32(x[4 * q + 3]));
+            float4* arow = (float4*)(base_ptr + DRING_BYTES + s * STAGE_BYTES + A_OFF + m * (KS * 4));
+            const int q0 = 2 * grp;
+            arow[q0 ^ ((m >> 1) & 3)] = make_float4(to_tf32(x[0]), to_tf32(x[1]), to_tf32(x[2]), to_tf32(x[3]));
+            arow[(q0 + 1) ^ ((m >> 1) & 3)] = make_float4(to_tf32(x[4]), to_tf32(x[5]), to_tf32(x[6]), to_tf32(x[7]));
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(afull_bar(s));
         }
-        const int m = box * 32 + lane;   // TMEM lane = local data column
+    }
+    __syncthreads();   // every role has left its loop: the staging ring is free
+    double* nsum = (double*)base_ptr;   // per column: the two 8-row groups' compensated sums of squares
+    if (copy_index(warp) >= 0) {
+        const int ci = copy_index(warp);
+        nsum[(ci >> 2) * TILE_M + (ci & 3) * 32 + lane] = (double)hi + (double)lo;
+    }
+    __syncthreads();
+    if (warp >= 4 && warp < 8) {
+        // ---------------- TMEM drain (warp w reads TMEM lanes 32 (w % 4) ...): add the tile into the split's partial
+        const int q = warp & 3;
+        const int m = q * 32 + lane;
         const bool acc_ok = __all_sync(0xffffffffu, !*abort_flag && mbar_wait(acc_bar, 0, abort_flag));
         if (acc_ok) {
             tc_fence_after();
@@ -381,14 +442,28 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
             float* dst = args.part + ((int64_t)split * args.ntot + c) * args.ldk;
             for (int cc = 0; cc < args.kc; cc += 32) {
                 float v[32];
-                tmem_ld32(tmem + ((uint32_t)(box * 32) << 16) + (uint32_t)cc, v);
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)cc, v);
                 if (m < valid) {
+                    if (args.ldk % 4 == 0) {
 #pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        if (cc + i < args.k) dst[cc + i] += v[i];
+                        for (int i = 0; i < 32; i += 4)
+                            if (cc + i < args.ldk) {
+                                float4* p4 = (float4*)(dst + cc + i);
+                                float4 o = *p4;
+                                o.x += v[i];
+                                o.y += v[i + 1];
+                                o.z += v[i + 2];
+                                o.w += v[i + 3];
+                                *p4 = o;
+                            }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            if (cc + i < args.k) dst[cc + i] += v[i];
+                    }
                 }
             }
-            if (m < valid) args.nsq[(int64_t)split * args.ntot + c] += (double)hi + (double)lo;
+            if (m < valid) args.nsq[(int64_t)split * args.ntot + c] += nsum[m] + nsum[TILE_M + m];
         } else if (lane == 0) {
             *abort_flag = 1;
             set_error(args.err, DEVERR_TIMEOUT | (1 << 11));
