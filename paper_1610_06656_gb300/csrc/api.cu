@@ -245,14 +245,13 @@ smp_status smp_sample_from_norms(smp_ctx* c, const double* sA, const double* sB,
     cudaError_t e = cudaMemcpyAsync(c->s_all, sA, (size_t)c->p.n1 * 8, cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess && !c->p.same_ab)
         e = cudaMemcpyAsync(c->s_all + c->p.n1, sB, (size_t)c->p.n2 * 8, cudaMemcpyDeviceToDevice, c->stream);
-    if (e != cudaSuccess) return check_cuda(c, e, "smp_sample_from_norms");
-    smp_status s = run_sample(c, m, seed, nnz_out);
-    if (s != SMP_OK) return s;
+    if (e == cudaSuccess) e = launch_frobenius(c);
     double F[2];
-    e = cudaMemcpy(F, c->F, 16, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(F, c->F, 16, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return check_cuda(c, e, "smp_sample_from_norms");
     if (!(F[0] > 0.0) && !(F[1] > 0.0)) return fail(c, SMP_EINVAL, "both Frobenius norms are zero");
-    return SMP_OK;
+    return run_sample(c, m, seed, nnz_out);
 }
 
 smp_status smp_omega_view(const smp_ctx* c, int64_t* nnz, const int64_t** row_ptr, const int32_t** col,

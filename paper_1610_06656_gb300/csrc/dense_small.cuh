@@ -6,6 +6,7 @@
 // the binary64 code paths use rsqrt_refined (binary32 estimate + Newton-Raphson) and multiply by reciprocals.
 #pragma once
 #include "common.cuh"
+#include "internal.h"
 
 namespace smp {
 
@@ -90,6 +91,61 @@ __global__ void chol_kernel(const double* __restrict__ G, int b, double* R, doub
     }
 }
 
+// Upper Cholesky factor of a b x b symmetric matrix (b <= 32) held in registers: lane i keeps row i of the matrix,
+// pivots and column entries travel by warp shuffles (right-looking elimination; the trailing updates of one column
+// are independent multiply-adds). Same pivot rule and output as chol_kernel. When nblk > 0, G is first formed as
+// the fixed-order sum of nblk partial Gram blocks part[blk][b * b] (the whole CTA reduces, warp 0 factors).
+__global__ void __launch_bounds__(256) chol32_kernel(const double* __restrict__ part, int nblk,
+                                                     const double* __restrict__ Gin, int b, double* R, double tol) {
+    __shared__ double Gs[32 * 32];
+    const double* G = Gin;
+    if (nblk > 0) {
+        const int npair = b * b;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int pq = warp; pq < npair; pq += (int)(blockDim.x >> 5)) {   // one warp per entry, as gram_reduce
+            double s = 0.0;
+            for (int k = lane; k < nblk; k += 32) s += part[(int64_t)k * npair + pq];
+            s = warp_sum(s);
+            if (lane == 0) Gs[pq] = s;
+        }
+        __syncthreads();
+        G = Gs;
+    }
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    double a[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) a[k] = (lane < b && k < b) ? G[lane * b + k] : 0.0;
+    double maxd = 0.0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+        if (k == lane && lane < b) maxd = a[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) maxd = fmax(maxd, __shfl_xor_sync(0xffffffffu, maxd, o));
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        if (j < b) {
+            const double d = __shfl_sync(0xffffffffu, a[j], j);
+            const bool ok = d > tol * maxd && d > 0.0;
+            const double y = ok ? rsqrt_refined(d) : 0.0;
+            const double lij = lane == j ? (ok ? d * y : 0.0) : (lane > j ? a[j] * y : 0.0);
+            if (lane >= j) a[j] = lij;
+#pragma unroll
+            for (int kk = j + 1; kk < 32; ++kk) {
+                if (kk < b) {
+                    const double lkj = __shfl_sync(0xffffffffu, lij, kk);   // L[kk][j]
+                    if (lane > j) a[kk] = fma(-lij, lkj, a[kk]);
+                }
+            }
+        }
+    }
+    if (lane < b) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+            if (k < b) R[k * b + lane] = k <= lane ? a[k] : 0.0;   // R = L^T
+    }
+}
+
 // X_out[i] = X_in[i] R^-1 (row vector times inverse upper factor), the substitution carried out in TC (binary32
 // for the subspace iteration's first Cholesky-QR pass, whose second pass restores orthogonality; binary64 for the
 // canonical form); a zero pivot zeroes that column.
@@ -136,9 +192,11 @@ __device__ __forceinline__ void jacobi_rotation(double app, double aqq, double a
 }
 
 // Symmetric eigen decomposition A = V diag(lambda) V^T (n <= MAX_SMALL) in precision T by cyclic Jacobi with
-// round-robin pairing (n/2 disjoint rotations per step, all applied in parallel). Stops when the off-diagonal
-// square sum (summed directly) is <= tol^2 times the diagonal's. Output (binary64): eigenvalues in decreasing
-// order and V's columns permuted to match. One CTA of 256 threads, dynamic shared memory 2 n (n + 1) sizeof(T).
+// round-robin pairing (n/2 disjoint rotations per step, all applied in parallel). A pair (p, q) is rotated only when
+// |A_pq| > tol (|A_pp| + |A_qq|) and |A_pq| > 8 eps_T ||A||_F (the negligibility test of the cyclic Jacobi method;
+// below it a rotation only stirs rounding noise); the method stops after a sweep that rotates no pair, or after
+// max_sweeps. tol must exceed a few eps_T. Output (binary64): eigenvalues in decreasing order and V's columns
+// permuted to match. One CTA of 256 threads, dynamic shared memory 2 n (n + 1) sizeof(T).
 template <typename T>
 __global__ void __launch_bounds__(256) jacobi_eig_kernel(const double* __restrict__ Ain, int n, double tol,
                                                          int max_sweeps, double* evals, double* Vout) {
@@ -147,43 +205,35 @@ __global__ void __launch_bounds__(256) jacobi_eig_kernel(const double* __restric
     T* V = A + n * (n + 1);          // n x (n+1)
     __shared__ int rp[MAX_SMALL / 2 + 1], rq[MAX_SMALL / 2 + 1];
     __shared__ T rc[MAX_SMALL / 2 + 1], rs[MAX_SMALL / 2 + 1];
-    __shared__ double red[8], red2[8];
-    __shared__ int stop;
+    __shared__ double red[8];
+    __shared__ double floor_abs;
+    __shared__ int rotated[3];       // per sweep (mod 3): did any pair rotate
     __shared__ int order[MAX_SMALL];
     const int ld = n + 1;
+    double fro = 0.0;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int i = e / n, j = e - i * n;
-        A[i * ld + j] = (T)Ain[e];
+        const double v = Ain[e];
+        A[i * ld + j] = (T)v;
         V[i * ld + j] = i == j ? T(1) : T(0);
+        fro += v * v;
+    }
+    fro = warp_sum(fro);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = fro;
+    if (threadIdx.x < 3) rotated[threadIdx.x] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double f = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) f += red[w];
+        const double eps = sizeof(T) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+        floor_abs = 8.0 * eps * sqrt(f);
     }
     __syncthreads();
+    const T tol_t = (T)tol, floor_t = (T)floor_abs;
     const int m = n + (n & 1);
     const int npairs = m / 2;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        double off = 0.0, dia = 0.0;
-        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-            const int i = e / n, j = e - i * n;
-            const double v = (double)A[i * ld + j];
-            if (i == j) dia += v * v;
-            else off += v * v;
-        }
-        off = warp_sum(off);
-        dia = warp_sum(dia);
-        if ((threadIdx.x & 31) == 0) {
-            red[threadIdx.x >> 5] = off;
-            red2[threadIdx.x >> 5] = dia;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double o = 0.0, d = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                o += red[w];
-                d += red2[w];
-            }
-            stop = o <= tol * tol * d;
-        }
-        __syncthreads();
-        if (stop) break;
+        if (threadIdx.x == 0) rotated[(sweep + 1) % 3] = 0;   // the flag the next sweep sets; nobody reads it now
         for (int s = 0; s < m - 1; ++s) {
             if (threadIdx.x < npairs) {
                 const int k = threadIdx.x;
@@ -196,12 +246,18 @@ __global__ void __launch_bounds__(256) jacobi_eig_kernel(const double* __restric
                     q = t;
                 }
                 T c = T(1), sn = T(0);
+                bool rot = false;
                 if (q < n) {
-                    const T apq = A[p * ld + q];
-                    if (apq != T(0)) jacobi_rotation(A[p * ld + p], A[q * ld + q], apq, c, sn);
-                } else {
-                    q = p;   // dummy player: no rotation
+                    const T apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
+                    const T aa = apq < T(0) ? -apq : apq;
+                    const T dd = (app < T(0) ? -app : app) + (aqq < T(0) ? -aqq : aqq);
+                    if (aa > floor_t && aa > tol_t * dd) {
+                        jacobi_rotation(app, aqq, apq, c, sn);
+                        rot = sn != T(0);   // an angle outside binary32 range comes back as the identity
+                        if (rot) rotated[sweep % 3] = 1;
+                    }
                 }
+                if (!rot) q = p;   // no rotation (dummy player or negligible entry)
                 rp[k] = p;
                 rq[k] = q;
                 rc[k] = c;
@@ -232,6 +288,7 @@ __global__ void __launch_bounds__(256) jacobi_eig_kernel(const double* __restric
             }
             __syncthreads();
         }
+        if (!rotated[sweep % 3]) break;
     }
     if (threadIdx.x < n) {   // stable sort, decreasing
         const int i = threadIdx.x;
@@ -249,6 +306,112 @@ __global__ void __launch_bounds__(256) jacobi_eig_kernel(const double* __restric
         Vout[e] = (double)V[i * ld + order[c]];
     }
     if (threadIdx.x < n) evals[threadIdx.x] = (double)A[order[threadIdx.x] * ld + order[threadIdx.x]];
+}
+
+// Symmetric eigen decomposition (jacobi_eig_kernel semantics). The 256-thread CTA keeps the four binary64 pipes of
+// the SM busy; a one-warp variant measured 2.3x slower in binary64 on this part.
+template <typename T>
+inline void launch_jacobi(const double* A, int n, double tol, int max_sweeps, double* evals, double* V,
+                          cudaStream_t st) {
+    jacobi_eig_kernel<T><<<smp::counted(1), 256, 2 * n * (n + 1) * (int)sizeof(T), st>>>(A, n, tol, max_sweeps,
+                                                                                         evals, V);
+}
+
+// Singular value decomposition K = W diag(S) Z^T of an r x r matrix (r <= 32) by one-sided (Hestenes) Jacobi in
+// binary64: column pairs (p, q) of U (initially K) are rotated until every pair is orthogonal to
+// |u_p . u_q| <= tol ||u_p|| ||u_q||; the rotations accumulate in Z; S_j = ||u_j||, W_j = u_j / S_j (a zero
+// singular value leaves a zero column of W). Pairs follow the round-robin order, one warp per pair, so each step's
+// n/2 rotations run in parallel; the sweep loop stops after a sweep without rotations or after max_sweeps. K is
+// scaled by a power of two (exact) so the binary32 angle computation stays in range. Output sorted by decreasing S.
+// One CTA of 256 threads.
+__global__ void __launch_bounds__(256) svd_onesided_kernel(const double* __restrict__ K, int r, double tol,
+                                                           int max_sweeps, double* S, double* W, double* Z) {
+    __shared__ double Us[32][33], Vs[32][33];
+    __shared__ double sig[32];
+    __shared__ double red[8];
+    __shared__ int order[32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double mx = 0.0;
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) mx = fmax(mx, fabs(K[e]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red[warp] = mx;
+    __syncthreads();
+    mx = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+    int ex = 0;
+    if (mx > 0.0) frexp(mx, &ex);
+    const double scale = ldexp(1.0, -ex), unscale = ldexp(1.0, ex);
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+        const int i = e / r, j = e - i * r;
+        Us[i][j] = K[e] * scale;
+        Vs[i][j] = i == j ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const int m = r + (r & 1);
+    const int npairs = m / 2;
+    const double tol2 = tol * tol;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        int any = 0;
+        for (int st = 0; st < m - 1; ++st) {
+            int my_rot = 0;
+            for (int k = warp; k < npairs; k += (int)(blockDim.x >> 5)) {
+                const int x0 = k, x1 = m - 1 - k;
+                int ip = x0 - 1 + st, iq = x1 - 1 + st;
+                if (ip >= m - 1) ip -= m - 1;
+                if (iq >= m - 1) iq -= m - 1;
+                int p = x0 == 0 ? 0 : 1 + ip;
+                int q = x1 == 0 ? 0 : 1 + iq;
+                if (p > q) {
+                    const int t = p;
+                    p = q;
+                    q = t;
+                }
+                if (q >= r) continue;
+                const double a = lane < r ? Us[lane][p] : 0.0;
+                const double b = lane < r ? Us[lane][q] : 0.0;
+                const double alpha = warp_sum(a * a), beta = warp_sum(b * b), gamma = warp_sum(a * b);
+                if (gamma != 0.0 && gamma * gamma > tol2 * alpha * beta) {
+                    double c, sn;
+                    jacobi_rotation(alpha, beta, gamma, c, sn);
+                    if (sn != 0.0) {
+                        if (lane < r) {
+                            Us[lane][p] = c * a - sn * b;
+                            Us[lane][q] = sn * a + c * b;
+                            const double vp = Vs[lane][p], vq = Vs[lane][q];
+                            Vs[lane][p] = c * vp - sn * vq;
+                            Vs[lane][q] = sn * vp + c * vq;
+                        }
+                        my_rot = 1;
+                    }
+                }
+            }
+            any |= __syncthreads_or(my_rot);
+        }
+        if (!any) break;
+    }
+    for (int j = warp; j < r; j += (int)(blockDim.x >> 5)) {
+        const double a = lane < r ? Us[lane][j] : 0.0;
+        const double n2 = warp_sum(a * a);
+        if (lane == 0) sig[j] = sqrt(n2);
+    }
+    __syncthreads();
+    if (threadIdx.x < r) {   // stable sort, decreasing
+        const int i = threadIdx.x;
+        const double si = sig[i];
+        int rank = 0;
+        for (int j = 0; j < r; ++j) rank += (sig[j] > si) || (sig[j] == si && j < i);
+        order[rank] = i;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+        const int i = e / r, cc = e - i * r;
+        const int j = order[cc];
+        const double sj = sig[j];
+        W[e] = sj > 0.0 ? Us[i][j] / sj : 0.0;
+        Z[e] = Vs[i][j];
+    }
+    if (threadIdx.x < r) S[threadIdx.x] = sig[order[threadIdx.x]] * unscale;
 }
 
 }  // namespace smp

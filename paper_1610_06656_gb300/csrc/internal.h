@@ -64,6 +64,7 @@ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 cudaError_t launch_sketch_simt(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t row0,
                                int64_t nrows, const void* Pi, int64_t ldp);
 cudaError_t launch_finalize(smp_ctx* c);
+cudaError_t launch_frobenius(smp_ctx* c);   // F[0], F[1] from s_all (left-to-right sums)
 cudaError_t launch_import(smp_ctx* c, const void* At, const void* Bt, const double* sA, const double* sB);
 cudaError_t launch_sketch_simt_into(int dtype, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1,
                                     int64_t n2, int k, uint64_t seed, int64_t row0, int64_t nrows, float* part,

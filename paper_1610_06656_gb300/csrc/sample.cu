@@ -5,7 +5,7 @@
 // step is a single round-to-nearest binary64 operation written with the _rn intrinsics (never contracted), so two
 // implementations that follow the same order draw the same Omega bit for bit.
 //
-// Pipeline: terms (alpha, beta, F) -> coin words (one warp per 32 columns of a row: ballot of the 32 coins,
+// Pipeline: terms (alpha, beta from F) -> coin words (one warp per 32 columns of a row: ballot of the 32 coins,
 // popcount per word, column counts) -> per-row prefix over words -> scans to row_ptr / col_ptr -> CSR fill from
 // the bit words -> CSC fill (one CTA per column, block scan over rows, CSR position from the word prefix).
 #include <algorithm>
@@ -17,31 +17,16 @@
 namespace smp {
 namespace {
 
+// alpha, beta from the column sums of squares and the Frobenius squares F (left-to-right sums, already in F).
 __global__ void terms_kernel(const double* __restrict__ s_all, int64_t n1, int64_t n2, int same_ab, double m,
-                             double* F, double* alpha, double* beta) {
-    __shared__ double fab[2];
-    if (threadIdx.x == 0) {
-        double fa = 0.0;
-        for (int64_t i = 0; i < n1; ++i) fa = __dadd_rn(fa, s_all[i]);
-        double fb = fa;
-        if (!same_ab) {
-            fb = 0.0;
-            for (int64_t j = 0; j < n2; ++j) fb = __dadd_rn(fb, s_all[n1 + j]);
-        }
-        fab[0] = fa;
-        fab[1] = fb;
-        F[0] = fa;
-        F[1] = fb;
-    }
-    __syncthreads();
-    const double fa = fab[0], fb = fab[1];
+                             const double* __restrict__ F, double* alpha, double* beta) {
+    const double fa = F[0], fb = F[1];
     const double* sB = same_ab ? s_all : s_all + n1;
     const double da = __dmul_rn((double)(2 * n2), fa);
     const double db = __dmul_rn((double)(2 * n1), fb);
-    for (int64_t i = threadIdx.x; i < n1; i += blockDim.x)
-        alpha[i] = fa > 0.0 ? __dmul_rn(m, __ddiv_rn(s_all[i], da)) : 0.0;
-    for (int64_t j = threadIdx.x; j < n2; j += blockDim.x)
-        beta[j] = fb > 0.0 ? __dmul_rn(m, __ddiv_rn(sB[j], db)) : 0.0;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n1) alpha[t] = fa > 0.0 ? __dmul_rn(m, __ddiv_rn(s_all[t], da)) : 0.0;
+    if (t < n2) beta[t] = fb > 0.0 ? __dmul_rn(m, __ddiv_rn(sB[t], db)) : 0.0;
 }
 
 __device__ __forceinline__ double qhat_of(double a, double b) {
@@ -241,7 +226,8 @@ smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out) {
         c->mask_words = n1 * W;
     }
     cudaError_t e;
-    terms_kernel<<<smp::counted(1), 256, 0, st>>>(c->s_all, n1, n2, c->p.same_ab, m, c->F, c->alpha, c->beta);
+    terms_kernel<<<smp::counted((unsigned)((std::max(n1, n2) + 255) / 256)), 256, 0, st>>>(c->s_all, n1, n2, c->p.same_ab, m,
+                                                                                    c->F, c->alpha, c->beta);
     if ((e = cudaMemsetAsync(c->col_cnt, 0, (size_t)n2 * 4, st)) != cudaSuccess) return check_cuda(c, e, "memset");
     const int64_t warps = n1 * W;
     const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);

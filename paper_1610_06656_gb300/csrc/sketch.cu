@@ -255,18 +255,20 @@ __global__ void __launch_bounds__(256) finalize_kernel(const TAcc* __restrict__ 
     }
 }
 
-// ||X||_F^2 summed strictly left to right (one thread): the order the sampler's reading fixes.
+// ||X||_F^2 summed strictly left to right: the order the sampler's reading fixes. ||A||_F^2 on thread 0 and
+// ||B||_F^2 on thread 32 (two warps, so the two dependent chains run side by side).
 __global__ void frobenius_kernel(const double* s_all, int64_t n1, int64_t n2, int same_ab, double* F) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double fa = 0.0;
-    for (int64_t i = 0; i < n1; ++i) fa = __dadd_rn(fa, s_all[i]);
-    double fb = fa;
-    if (!same_ab) {
-        fb = 0.0;
+    if (blockIdx.x != 0) return;
+    if (threadIdx.x == 0) {
+        double fa = 0.0;
+        for (int64_t i = 0; i < n1; ++i) fa = __dadd_rn(fa, s_all[i]);
+        F[0] = fa;
+        if (same_ab) F[1] = fa;
+    } else if (threadIdx.x == 32 && !same_ab) {
+        double fb = 0.0;
         for (int64_t j = 0; j < n2; ++j) fb = __dadd_rn(fb, s_all[n1 + j]);
+        F[1] = fb;
     }
-    F[0] = fa;
-    F[1] = fb;
 }
 
 // Import: copy caller sketch columns (n x k, dense) into the padded layout and recompute D.
@@ -308,6 +310,11 @@ cudaError_t launch_sketch_simt(smp_ctx* c, const void* A, int64_t lda, const voi
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_frobenius(smp_ctx* c) {
+    frobenius_kernel<<<smp::counted(1), 64, 0, c->stream>>>(c->s_all, c->p.n1, c->p.n2, c->p.same_ab, c->F);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(smp_ctx* c) {
     const unsigned nb = (unsigned)c->ntot;
     if (c->acc_bytes == 8)
@@ -316,7 +323,7 @@ cudaError_t launch_finalize(smp_ctx* c) {
     else
         finalize_kernel<float><<<smp::counted(nb), 256, 0, c->stream>>>((const float*)c->part, c->nsq, c->splits, c->ntot,
                                                          c->p.k, c->ldk, (float*)c->sk, c->s_all, c->D_all);
-    frobenius_kernel<<<smp::counted(1), 32, 0, c->stream>>>(c->s_all, c->p.n1, c->p.n2, c->p.same_ab, c->F);
+    frobenius_kernel<<<smp::counted(1), 64, 0, c->stream>>>(c->s_all, c->p.n1, c->p.n2, c->p.same_ab, c->F);
     return cudaGetLastError();
 }
 
@@ -331,7 +338,7 @@ cudaError_t launch_import(smp_ctx* c, const void* At, const void* Bt, const doub
     else
         import_kernel<float><<<smp::counted(nb), 256, 0, c->stream>>>((const float*)At, (const float*)bt, c->p.n1, c->ntot,
                                                        c->p.k, c->ldk, (float*)c->sk, sA, sb, c->s_all, c->D_all);
-    frobenius_kernel<<<smp::counted(1), 32, 0, c->stream>>>(c->s_all, c->p.n1, c->p.n2, c->p.same_ab, c->F);
+    frobenius_kernel<<<smp::counted(1), 64, 0, c->stream>>>(c->s_all, c->p.n1, c->p.n2, c->p.same_ab, c->F);
     return cudaGetLastError();
 }
 

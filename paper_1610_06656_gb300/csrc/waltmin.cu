@@ -373,43 +373,14 @@ constexpr int solve_smem_bytes() {
 // ---------------------------------------------------------------------------------------------------------------
 // canonical form
 // ---------------------------------------------------------------------------------------------------------------
-// K = Ru Rv^T and the augmented symmetric H = [[0, K], [K^T, 0]] (2r x 2r).
-__global__ void core_kernel(const double* __restrict__ Ru, const double* __restrict__ Rv, int r, double* H) {
+// K = Ru Rv^T (r x r), the core whose SVD gives the canonical form.
+__global__ void core_kernel(const double* __restrict__ Ru, const double* __restrict__ Rv, int r, double* K) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = 2 * r;
-    if (e >= n * n) return;
-    const int i = e / n, j = e - i * n;
+    if (e >= r * r) return;
+    const int i = e / r, j = e - i * r;
     double v = 0.0;
-    if (i < r && j >= r) {
-        const int jj = j - r;
-        for (int l = 0; l < r; ++l) v += Ru[i * r + l] * Rv[jj * r + l];
-    } else if (i >= r && j < r) {
-        const int ii = i - r;
-        for (int l = 0; l < r; ++l) v += Ru[j * r + l] * Rv[ii * r + l];
-    }
-    H[e] = v;
-}
-
-// From the eigenvectors of H (2r x 2r, sorted decreasing): S[c] = lambda_c, W = top block, Z = bottom block of the
-// first r eigenvectors, each renormalised (a zero singular value leaves a zero column).
-__global__ void core_split_kernel(const double* __restrict__ ev, const double* __restrict__ EV, int r, double* S,
-                                  double* Wc, double* Zc) {
-    const int c = threadIdx.x;
-    if (c >= r) return;
-    const int n = 2 * r;
-    double nu = 0.0, nv = 0.0;
-    for (int i = 0; i < r; ++i) {
-        nu += EV[i * n + c] * EV[i * n + c];
-        nv += EV[(r + i) * n + c] * EV[(r + i) * n + c];
-    }
-    const double lam = ev[c];
-    const double iu = (lam > 0.0 && nu > 0.0) ? rsqrt_refined(nu) : 0.0;
-    const double iv = (lam > 0.0 && nv > 0.0) ? rsqrt_refined(nv) : 0.0;
-    S[c] = lam > 0.0 ? lam : 0.0;
-    for (int i = 0; i < r; ++i) {
-        Wc[i * r + c] = EV[i * n + c] * iu;
-        Zc[i * r + c] = EV[(r + i) * n + c] * iv;
-    }
+    for (int l = 0; l < r; ++l) v = fma(Ru[i * r + l], Rv[j * r + l], v);
+    K[e] = v;
 }
 
 // X_out (n x r) = Q (n x r) * Wc (r x r)
@@ -495,14 +466,25 @@ void gram(const TX* X, const TY* Y, int64_t n, int a, int b, double* part, doubl
 
 // Cholesky-QR twice: Q = X R^-1 with X = Q R; Rout = R2 R1 (upper). Q may alias X. The Gram matrices and the
 // factorisations are binary64; the substitutions run in TC.
+// Upper Cholesky factor R of the Gram matrix X^T X (X: n x b): partial Gram blocks, their fixed-order reduction,
+// then the register Cholesky (b <= 32) or the shared-memory one.
+template <typename TX>
+void gram_chol(const TX* X, int64_t n, int b, double* part, double* G, double* R, cudaStream_t st) {
+    const int nblk = (int)std::max<int64_t>(1, (n + GRAM_ROWS_PER_BLOCK - 1) / GRAM_ROWS_PER_BLOCK);
+    gram_partial_kernel<TX, TX><<<smp::counted(nblk), 256, 0, st>>>(X, X, n, b, b, part);
+    gram_reduce_kernel<<<smp::counted(nblocks(b * b * 32, 256)), 256, 0, st>>>(part, nblk, b * b, G);
+    if (b <= 32)
+        chol32_kernel<<<smp::counted(1), 32, 0, st>>>(nullptr, 0, G, b, R, 1e-28);
+    else
+        chol_kernel<<<smp::counted(1), 32, 0, st>>>(G, b, R, 1e-28);
+}
+
 template <typename TX, typename TQ, typename TC>
 void cholqr2(const TX* X, int64_t n, int b, TQ* Q, double* part, double* G, double* R1, double* R2, double* Rout,
              cudaStream_t st) {
-    gram<TX, TX>(X, X, n, b, b, part, G, st);
-    chol_kernel<<<smp::counted(1), 32, 0, st>>>(G, b, R1, 1e-28);
+    gram_chol<TX>(X, n, b, part, G, R1, st);
     apply_rinv_kernel<TX, TQ, TC><<<smp::counted(nblocks(n, 128)), 128, 0, st>>>(X, n, b, R1, Q);
-    gram<TQ, TQ>(Q, Q, n, b, b, part, G, st);
-    chol_kernel<<<smp::counted(1), 32, 0, st>>>(G, b, R2, 1e-28);
+    gram_chol<TQ>(Q, n, b, part, G, R2, st);
     apply_rinv_kernel<TQ, TQ, TC><<<smp::counted(nblocks(n, 128)), 128, 0, st>>>(Q, n, b, R2, Q);
     if (Rout) upper_mul_kernel<<<smp::counted(nblocks(b * b, 256)), 256, 0, st>>>(R2, R1, b, Rout);
 }
@@ -582,7 +564,7 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
     add(n2 * r, sizeof(TF));                 // Vf
     add(n1 * r, 8);                          // Qu
     add(n2 * r, 8);                          // Qv
-    add(12 * r * r + 8 * r, 8);              // Ru, Rv, H, EV, W, Z, ...
+    add(12 * r * r + 8 * r, 8);              // Ru, Rv, K, W, Z, ...
     add(n1 + n2 + 2, 4);                     // segment counts
     add(n1 + n2 + 4, 8);                     // segment starts
     add(4 * nseg_max, 8);                    // segment begins / ends
@@ -613,8 +595,6 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
     double* Ru = ar.take<double>(r * r);
     double* Rv = ar.take<double>(r * r);
     double* H = ar.take<double>(4 * r * r);
-    double* EV = ar.take<double>(4 * r * r);
-    double* evh = ar.take<double>(2 * r);
     double* Wc = ar.take<double>(r * r);
     double* Zc = ar.take<double>(r * r);
     double* Rx1 = ar.take<double>(r * r);
@@ -665,9 +645,6 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
     if (split && nnz > 0)
         split_kernel<<<smp::counted(nblocks(nnz, 256)), 256, 0, st>>>(c->erow, c->col, nnz, T, k0, k1, sub);
     const uint8_t* subp = split ? sub : nullptr;
-    auto jacobi64 = [&](const double* Ain, int n, double tol, double* evals, double* Vout) {
-        jacobi_eig_kernel<double><<<smp::counted(1), 256, 2 * n * (n + 1) * 8, st>>>(Ain, n, tol, 40, evals, Vout);
-    };
     smp_status status = SMP_OK;
     if (flags & SMP_INIT_GIVEN) {
         convert_kernel<double, TF><<<smp::counted(nblocks(n1 * r, 256)), 256, 0, st>>>(U_init, n1 * r, Uf);
@@ -694,7 +671,7 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
             gram<TY, TY>(Z, Z, n2, b, b, part, G, st);
             bool done = false;
             if (dbl) {
-                jacobi_eig_kernel<double><<<smp::counted(1), 256, 2 * b * (b + 1) * 8, st>>>(G, b, 1e-15, 40, ev, E);
+                launch_jacobi<double>(G, b, 4e-15, 40, ev, E, st);
                 ritz_kernel<TY><<<smp::counted(nblocks(n1 * r, 256)), 256, 0, st>>>(Y, E, n1, b, r, U0);
                 if (have_prev) {
                     gram<double, double>(U0, U0p, n1, r, r, part, Gx, st);
@@ -712,7 +689,7 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
                 }
                 cudaMemcpyAsync(U0p, U0, sizeof(double) * n1 * r, cudaMemcpyDeviceToDevice, st);
             } else {
-                jacobi_eig_kernel<float><<<smp::counted(1), 256, 2 * b * (b + 1) * 4, st>>>(G, b, 1e-7, 30, ev, E);
+                launch_jacobi<float>(G, b, 1e-6, 30, ev, E, st);
                 cudaError_t e1 = cudaMemcpyAsync(cur_ev.data(), ev, sizeof(double) * b, cudaMemcpyDeviceToHost, st);
                 if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(st);
                 if (e1 != cudaSuccess) {
@@ -729,11 +706,8 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
             }
             have_prev = true;
             if (done || it == max_iter) {
-                if (!dbl) {   // final Rayleigh-Ritz vectors in binary64
-                    jacobi_eig_kernel<double><<<smp::counted(1), 256, 2 * b * (b + 1) * 8, st>>>(G, b, 1e-15, 40, ev,
-                                                                                                E);
+                if (!dbl)   // Rayleigh-Ritz vectors from the binary32 eigenvectors of the last check
                     ritz_kernel<TY><<<smp::counted(nblocks(n1 * r, 256)), 256, 0, st>>>(Y, E, n1, b, r, U0);
-                }
                 break;
             }
         }
@@ -754,9 +728,8 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
         // canonical form
         cholqr2<TF, double, double>(Uf, n1, r, Qu, part, Gx, Rx1, Rx2, Ru, st);
         cholqr2<TF, double, double>(Vf, n2, r, Qv, part, Gx, Rx1, Rx2, Rv, st);
-        core_kernel<<<smp::counted(nblocks(4 * r * r, 256)), 256, 0, st>>>(Ru, Rv, r, H);
-        jacobi64(H, 2 * r, 1e-16, evh, EV);
-        core_split_kernel<<<smp::counted(1), 32, 0, st>>>(evh, EV, r, S, Wc, Zc);
+        core_kernel<<<smp::counted(nblocks(r * r, 256)), 256, 0, st>>>(Ru, Rv, r, H);
+        svd_onesided_kernel<<<smp::counted(1), 256, 0, st>>>(H, r, 4e-15, 40, S, Wc, Zc);
         small_right_mul_kernel<<<smp::counted(nblocks(n1 * r, 256)), 256, 0, st>>>(Qu, Wc, n1, r, U);
         small_right_mul_kernel<<<smp::counted(nblocks(n2 * r, 256)), 256, 0, st>>>(Qv, Zc, n2, r, V);
         sign_kernel<<<smp::counted(r), 256, 0, st>>>(U, n1, V, n2, r);
