@@ -267,7 +267,9 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
     // accumulator-ready barrier, the TMEM address word and the abort flag
     uint32_t* tmem_slot = (uint32_t*)(bars + 2 * DSTAGES + 3 * STAGES + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-    float hi = 0.f, lo = 0.f;             // copy warps: compensated sum of squares of their column and row group
+    // copy warps: compensated sums of squares of their column and row group, even and odd rows apart (two short
+    // dependency chains instead of one long one)
+    float hi0 = 0.f, lo0 = 0.f, hi1 = 0.f, lo1 = 0.f;
     auto dfull_bar = [&](int d) { return bar_base + 8u * d; };
     auto dempty_bar = [&](int d) { return bar_base + 8u * (DSTAGES + d); };
     auto pfull_bar = [&](int s) { return bar_base + 8u * (2 * DSTAGES + s); };
@@ -322,6 +324,16 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
                                     t + 8 * g, dfull_bar(d));
             }
             __syncwarp();
+        }
+        // the TMEM drain reads and rewrites this tile's slice of the split's partial sketch: bring it into L2 while
+        // the last stages are still in flight
+        {
+            const int nlines = (int)((args.ldk * 4 + 127) / 128);   // 128-byte lines per partial row (may overhang)
+            for (int e = lane; e < valid * nlines; e += 32) {
+                const int m = e / nlines, l = e - m * nlines;
+                const char* pr = (const char*)(args.part + ((int64_t)split * args.ntot + cbase + m) * args.ldk) + l * 128;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(pr));
+            }
         }
     } else if (warp == 2) {
         // ---------------- Pi producer: Pi tiles into the main ring once the MMA has released the stage
@@ -413,7 +425,10 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
             __syncwarp();
             if (lane == 0) mbar_arrive(dempty_bar(d));   // staging read: the producer may refill it
 #pragma unroll
-            for (int t = 0; t < 8; ++t) two_sum_square<float>(x[t], hi, lo);
+            for (int t = 0; t < 8; t += 2) {
+                two_sum_square<float>(x[t], hi0, lo0);
+                two_sum_square<float>(x[t + 1], hi1, lo1);
+            }
             // K-major copy: data column m is row m (64 B = KS values); 64B swizzle puts chunk q at q ^ ((m >> 1) & 3)
             float4* arow = (float4*)(base_ptr + DRING_BYTES + s * STAGE_BYTES + A_OFF + m * (KS * 4));
             const int q0 = 2 * grp;
@@ -428,19 +443,22 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
     double* nsum = (double*)base_ptr;   // per column: the two 8-row groups' compensated sums of squares
     if (copy_index(warp) >= 0) {
         const int ci = copy_index(warp);
-        nsum[(ci >> 2) * TILE_M + (ci & 3) * 32 + lane] = (double)hi + (double)lo;
+        nsum[(ci >> 2) * TILE_M + (ci & 3) * 32 + lane] = ((double)hi0 + (double)lo0) + ((double)hi1 + (double)lo1);
     }
     __syncthreads();
-    if (warp >= 4 && warp < 8) {
-        // ---------------- TMEM drain (warp w reads TMEM lanes 32 (w % 4) ...): add the tile into the split's partial
+    {
+        // ---------------- TMEM drain by all 16 warps: warp w reads TMEM lanes 32 (w % 4) ... and the column quarter
+        // w / 4 of the accumulator, and adds it into the split's partial sketch
         const int q = warp & 3;
         const int m = q * 32 + lane;
+        const int cq = ((args.kc / 32 + 3) / 4) * 32;   // accumulator columns per warp (multiple of 32)
+        const int cbeg = (warp >> 2) * cq, cend = min(args.kc, cbeg + cq);
         const bool acc_ok = __all_sync(0xffffffffu, !*abort_flag && mbar_wait(acc_bar, 0, abort_flag));
         if (acc_ok) {
             tc_fence_after();
             const int64_t c = cbase + m;
             float* dst = args.part + ((int64_t)split * args.ntot + c) * args.ldk;
-            for (int cc = 0; cc < args.kc; cc += 32) {
+            for (int cc = cbeg; cc < cend; cc += 32) {
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)cc, v);
                 if (m < valid) {
@@ -463,7 +481,7 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
                     }
                 }
             }
-            if (m < valid) args.nsq[(int64_t)split * args.ntot + c] += nsum[m] + nsum[TILE_M + m];
+            if (warp < 4 && m < valid) args.nsq[(int64_t)split * args.ntot + c] += nsum[m] + nsum[TILE_M + m];
         } else if (lane == 0) {
             *abort_flag = 1;
             set_error(args.err, DEVERR_TIMEOUT | (1 << 11));
