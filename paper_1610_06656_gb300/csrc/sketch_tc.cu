@@ -181,15 +181,47 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-template <typename T>
-__device__ __forceinline__ void two_sum_square(float x, float& hi, float& lo) {
-    const float p = __fmul_rn(x, x);
-    const float e = __fmaf_rn(x, x, -p);
-    const float s = __fadd_rn(hi, p);
-    const float bp = __fsub_rn(s, hi);
-    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
-    hi = s;
-    lo = __fadd_rn(lo, __fadd_rn(err, e));
+
+// Packed binary32 pairs (f32x2: two independent IEEE round-to-nearest lanes per instruction).
+__device__ __forceinline__ uint64_t pack2(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void unpack2(uint64_t r, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// Compensated accumulation of x^2 into (hi, lo), on two independent accumulators at once (lane by lane): the
+// product's rounding error comes from an FMA, the sum's from TwoSum (Knuth), and both are folded into lo.
+__device__ __forceinline__ void two_sum_square_x2(uint64_t x, uint64_t& hi, uint64_t& lo) {
+    const uint64_t p = mul2(x, x);
+    const uint64_t e = fma2(x, x, p ^ 0x8000000080000000ull);   // x*x - p exactly (sign flip of both lanes)
+    const uint64_t s2 = add2(hi, p);
+    const uint64_t bp = sub2(s2, hi);
+    const uint64_t err = add2(sub2(hi, sub2(s2, bp)), sub2(p, bp));
+    hi = s2;
+    lo = add2(lo, add2(err, e));
 }
 
 // ------------------------------------------------------------------------------------------------ Pi generation
@@ -267,9 +299,9 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
     // accumulator-ready barrier, the TMEM address word and the abort flag
     uint32_t* tmem_slot = (uint32_t*)(bars + 2 * DSTAGES + 3 * STAGES + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-    // copy warps: compensated sums of squares of their column and row group, even and odd rows apart (two short
-    // dependency chains instead of one long one)
-    float hi0 = 0.f, lo0 = 0.f, hi1 = 0.f, lo1 = 0.f;
+    // copy warps: compensated sums of squares of their column and row group, even and odd rows in the two lanes of
+    // packed f32x2 accumulators (two short dependency chains, half the instructions)
+    uint64_t hi2 = 0ull, lo2 = 0ull;
     auto dfull_bar = [&](int d) { return bar_base + 8u * d; };
     auto dempty_bar = [&](int d) { return bar_base + 8u * (DSTAGES + d); };
     auto pfull_bar = [&](int s) { return bar_base + 8u * (2 * DSTAGES + s); };
@@ -425,10 +457,7 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
             __syncwarp();
             if (lane == 0) mbar_arrive(dempty_bar(d));   // staging read: the producer may refill it
 #pragma unroll
-            for (int t = 0; t < 8; t += 2) {
-                two_sum_square<float>(x[t], hi0, lo0);
-                two_sum_square<float>(x[t + 1], hi1, lo1);
-            }
+            for (int t = 0; t < 8; t += 2) two_sum_square_x2(pack2(x[t], x[t + 1]), hi2, lo2);
             // K-major copy: data column m is row m (64 B = KS values); 64B swizzle puts chunk q at q ^ ((m >> 1) & 3)
             float4* arow = (float4*)(base_ptr + DRING_BYTES + s * STAGE_BYTES + A_OFF + m * (KS * 4));
             const int q0 = 2 * grp;
@@ -443,6 +472,9 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
     double* nsum = (double*)base_ptr;   // per column: the two 8-row groups' compensated sums of squares
     if (copy_index(warp) >= 0) {
         const int ci = copy_index(warp);
+        float hi0, hi1, lo0, lo1;
+        unpack2(hi2, hi0, hi1);
+        unpack2(lo2, lo0, lo1);
         nsum[(ci >> 2) * TILE_M + (ci & 3) * 32 + lane] = ((double)hi0 + (double)lo0) + ((double)hi1 + (double)lo1);
     }
     __syncthreads();
