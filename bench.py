@@ -29,6 +29,8 @@ METRIC = "sketch GB/s vs HBM peak; end-to-end solves/s & p99 at fixed spectral e
 WORKLOADS = {
     "scale": dict(d=1_000_000, n1=2000, n2=2000, L=20, sigma=0.1, alpha=0.5, k=500, r=10, T=10, block=65536),
     "tiny": dict(d=2000, n1=200, n2=200, L=10, sigma=0.1, alpha=0.5, k=100, r=5, T=10, block=65536),
+    # one 65,536-row block of the scale shape (1 GB of inputs): the case the ncu captures of the sketch kernel use
+    "block": dict(d=65536, n1=2000, n2=2000, L=20, sigma=0.1, alpha=0.5, k=500, r=10, T=10, block=65536),
 }
 
 
@@ -87,6 +89,14 @@ class ClockSampler:
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (every rank gets it): a step's time is the slowest rank's."""
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def dist_setup():
@@ -243,9 +253,7 @@ def main():
     clk = clocks.stop()
     elapsed = t_start.elapsed_time(t_end) / 1e3
     if world > 1:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+        elapsed = max_over_ranks(elapsed, dist, dev)
     step_ms = sorted(a.elapsed_time(b) for a, b in step_events)
     sk_ms = [a.elapsed_time(b) for a, b, _ in sk_events]
     sk_rows = [n for _, _, n in sk_events]
@@ -267,7 +275,7 @@ def main():
         roof = {"bound": "alu", "achieved": sk_flops / sk_avg_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
                 "peak_kind": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x %.0f MHz" % clk_mhz}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = sketch_traffic(sum(sk_rows) / len(sk_rows)) if tc_used else None
     roof["kernel"] = "pi_gen_kernel + sketch_tc_kernel (tcgen05)" if tc_used else "sketch_simt_kernel"
     roof["hbm_gbs"] = sk_bytes / sk_avg_s / 1e9
     roof["hbm_frac"] = roof["hbm_gbs"] / peaks["hbm_gbs"]
@@ -290,6 +298,8 @@ def main():
                "sample": "single pass over 16,384 of 1,000,000 rows (time x d/rows) + sampling, estimate and "
                          "WAltMin at n = 2,000; %.1f s of CPU wall time" % wall}
 
+    in_gb = w["d"] * (w["n1"] + w["n2"]) * 4 / 1e9
+    l2_note = ("inputs (%.1f GB) larger than L2; no flush" % in_gb) if in_gb > 0.129 else "inputs fit in L2"
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
@@ -297,7 +307,7 @@ def main():
                 "data": "synthetic (low rank 20 + noise 0.1, column scales (j+1)^-0.5, torch RNG seeded per rank)",
                 "config": {"workload": args.workload, **{k: w[k] for k in ("d", "n1", "n2", "k", "r", "T")},
                            "block_rows": w["block"], "m": m, "nnz": int(nnz), "parallelism": "replicas",
-                           "l2": "inputs (16 GB) larger than L2; no flush", "engine": args.engine},
+                           "l2": l2_note, "engine": args.engine},
                 "p50_ms": statistics.median(step_ms), "p99_ms": step_ms[min(len(step_ms) - 1,
                                                                             int(math.ceil(0.99 * len(step_ms))) - 1)],
                 "sketch_gbs": roof["hbm_gbs"], "spectral_err": err, "optimal_err": opt_err,
@@ -308,6 +318,23 @@ def main():
         dist.barrier()
         dist.destroy_process_group()
     solver.close()
+
+
+def sketch_traffic(rows_per_launch):
+    """DRAM bytes (read + write) per sketch launch from the committed ncu capture of sketch_tc_kernel, scaled to the
+    rows one launch of this run processes; None when the kernel source has changed since the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "sketch_tc_full_scale.md")) as f:
+            line = next(ln for ln in f if ln.startswith("bench: "))
+        kv = dict(tok.split("=") for tok in line.split()[1:])
+        with open(os.path.join(ROOT, "paper_1610_06656_gb300", "csrc", "sketch_tc.cu"), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    except (OSError, StopIteration, ValueError):
+        return None
+    if kv.get("sha") != sha:
+        return None
+    return float(kv["traffic_bytes"]) * rows_per_launch / float(kv["rows"])
 
 
 def tc_active(smp):
@@ -366,9 +393,7 @@ def run_e2e(torch, smp, solver, A, B, w, m, rank, steps, stream, world, dev):
     el = time.perf_counter() - t0
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([el], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
+        el = max_over_ranks(el, dist, dev)
     h2d = (A.numel() * A.element_size() + B.numel() * B.element_size())
     d2h = (outU.numel() + outS.numel() + outV.numel()) * 8
     return {"value": world * steps / el, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
