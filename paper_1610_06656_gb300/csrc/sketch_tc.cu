@@ -32,8 +32,21 @@ namespace {
 
 constexpr int TILE_M = 128;        // data columns per CTA (MMA M)
 constexpr int KS = 16;             // data rows per pipeline stage (two K = 8 MMA slices)
-constexpr int STAGES = 4;          // ring of (K-major data copy, Pi tile) consumed by the MMA
-constexpr int DSTAGES = 8;         // deeper ring of staged data tiles (TMA target), freed by the copy warps
+#ifndef SMP_TC_PSTAGES
+#define SMP_TC_PSTAGES 4
+#endif
+#ifndef SMP_TC_ASTAGES
+#define SMP_TC_ASTAGES 4
+#endif
+#ifndef SMP_TC_DSTAGES
+#define SMP_TC_DSTAGES 8
+#endif
+// Three rings: staged data tiles (TMA target, freed by the copy warps), K-major TF32 copies (written by the copy
+// warps, freed by the MMA) and Pi tiles (TMA target, freed by the MMA). The Pi ring is the deepest: a Pi stage
+// comes from L2 in ~1.3 us.
+constexpr int PSTAGES = SMP_TC_PSTAGES;
+constexpr int ASTAGES = SMP_TC_ASTAGES;
+constexpr int DSTAGES = SMP_TC_DSTAGES;
 constexpr int PI_BOX_ROWS = 256;   // sketch rows per Pi box (MMA N)
 constexpr int MAX_KC = 512;        // sketch rows per CTA (TMEM columns)
 constexpr int DATA_BOX_ROWS = 8;
@@ -42,12 +55,12 @@ constexpr int DATA_STAGE_BYTES = 4 * KS * 32 * 4;           // 128 columns x KS 
 constexpr int KGROUP_BYTES = 4 * DATA_BOX_BYTES;            // one 8-row group of all four boxes
 constexpr int A_STAGE_BYTES = TILE_M * KS * 4;             // K-major copy: 128 rows x 64 B (64-byte swizzle)
 constexpr int PI_BOX_BYTES = PI_BOX_ROWS * KS * 4;          // 256 rows x KS fp32
-constexpr int PI_STAGE_BYTES = 2 * PI_BOX_BYTES;
-constexpr int A_OFF = 0;                                    // offsets inside a main-ring stage
-constexpr int PI_OFF = A_STAGE_BYTES;
-constexpr int STAGE_BYTES = A_STAGE_BYTES + PI_STAGE_BYTES;
+constexpr int PI_STAGE_BYTES = (MAX_KC / PI_BOX_ROWS) * PI_BOX_BYTES;
 constexpr int DRING_BYTES = DSTAGES * DATA_STAGE_BYTES;
-constexpr int SMEM_BYTES = DRING_BYTES + STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+constexpr int ARING_BYTES = ASTAGES * A_STAGE_BYTES;
+constexpr int PRING_BYTES = PSTAGES * PI_STAGE_BYTES;
+constexpr int SMEM_BYTES = DRING_BYTES + ARING_BYTES + PRING_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 constexpr int THREADS = 512;       // 16 warps: producers 0 and 2, MMA 1, copy warps on schedulers 0, 2, 3
 constexpr int NCOPY = 8;           // copy warps: (32-column box, 8-row group) pairs
 // copy warp c (0..7) is warp COPY_WARP[c]: warp ids 4, 6, 7, 8, 10, 11, 12, 14 live on schedulers 0, 2, 3 (id % 4),
@@ -90,12 +103,15 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// One bounded try_wait: the thread may sleep in the hardware until the phase completes or SUSPEND_NS pass (a
+// polling loop without the hint spends issue slots and shared-memory cycles the copy warps and the MMA need).
+constexpr uint32_t SUSPEND_NS = 20000;
 __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(SUSPEND_NS)
         : "memory");
     return ok != 0;
 }
@@ -104,12 +120,10 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
     if (mbar_test(bar, parity)) return true;
     const unsigned long long t0 = global_timer();
-    for (uint32_t i = 1;; ++i) {
+    for (;;) {
         if (mbar_test(bar, parity)) return true;
-        if ((i & 255u) == 0) {
-            if (*abort_flag) return false;
-            if (global_timer() - t0 > WAIT_NS) return false;
-        }
+        if (*abort_flag) return false;
+        if (global_timer() - t0 > WAIT_NS) return false;
     }
 }
 
@@ -287,37 +301,42 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
     const int64_t cbase = on_b ? args.n1 + col0 : col0;
     const CUtensorMap* tm_data = on_b ? &tm_b : &tm_a;
 
-    // carve shared memory (1024-byte aligned): data ring, main ring, then barriers
+    // carve shared memory (1024-byte aligned): data ring, copy ring, Pi ring, then barriers
     const uint32_t raw = smem_addr(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t* base_ptr = smem_raw + (base - raw);
     const uint32_t dring = base;                        // DSTAGES x DATA_STAGE_BYTES
-    const uint32_t mring = base + DRING_BYTES;          // STAGES x STAGE_BYTES
-    const uint32_t bar_base = mring + STAGES * STAGE_BYTES;
-    uint64_t* bars = (uint64_t*)(base_ptr + DRING_BYTES + STAGES * STAGE_BYTES);
-    // bars: [0, D) data full, [D, 2D) data empty, then per main stage: Pi full, copy full, stage empty; then the
-    // accumulator-ready barrier, the TMEM address word and the abort flag
-    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * DSTAGES + 3 * STAGES + 1);
+    const uint32_t aring = base + DRING_BYTES;          // ASTAGES x A_STAGE_BYTES
+    const uint32_t pring = aring + ARING_BYTES;         // PSTAGES x PI_STAGE_BYTES
+    const uint32_t bar_base = pring + PRING_BYTES;
+    uint64_t* bars = (uint64_t*)(base_ptr + DRING_BYTES + ARING_BYTES + PRING_BYTES);
+    // bars: data full / empty [D], copy full / empty [A], Pi full / empty [P]; then the accumulator-ready barrier,
+    // the TMEM address word and the abort flag
+    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * (DSTAGES + ASTAGES + PSTAGES) + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     // copy warps: compensated sums of squares of their column and row group, even and odd rows in the two lanes of
     // packed f32x2 accumulators (two short dependency chains, half the instructions)
     uint64_t hi2 = 0ull, lo2 = 0ull;
     auto dfull_bar = [&](int d) { return bar_base + 8u * d; };
     auto dempty_bar = [&](int d) { return bar_base + 8u * (DSTAGES + d); };
-    auto pfull_bar = [&](int s) { return bar_base + 8u * (2 * DSTAGES + s); };
-    auto afull_bar = [&](int s) { return bar_base + 8u * (2 * DSTAGES + STAGES + s); };
-    auto empty_bar = [&](int s) { return bar_base + 8u * (2 * DSTAGES + 2 * STAGES + s); };
-    const uint32_t acc_bar = bar_base + 8u * (2 * DSTAGES + 3 * STAGES);
+    auto afull_bar = [&](int s) { return bar_base + 8u * (2 * DSTAGES + s); };
+    auto aempty_bar = [&](int s) { return bar_base + 8u * (2 * DSTAGES + ASTAGES + s); };
+    auto pfull_bar = [&](int s) { return bar_base + 8u * (2 * DSTAGES + 2 * ASTAGES + s); };
+    auto pempty_bar = [&](int s) { return bar_base + 8u * (2 * DSTAGES + 2 * ASTAGES + PSTAGES + s); };
+    const uint32_t acc_bar = bar_base + 8u * (2 * DSTAGES + 2 * ASTAGES + 2 * PSTAGES);
 
     if (threadIdx.x == 0) {
         for (int d = 0; d < DSTAGES; ++d) {
             mbar_init(dfull_bar(d), 1);
             mbar_init(dempty_bar(d), NCOPY);
         }
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(pfull_bar(s), 1);
+        for (int s = 0; s < ASTAGES; ++s) {
             mbar_init(afull_bar(s), NCOPY);
-            mbar_init(empty_bar(s), 1);       // the MMA commit
+            mbar_init(aempty_bar(s), 1);      // the MMA commit
+        }
+        for (int s = 0; s < PSTAGES; ++s) {
+            mbar_init(pfull_bar(s), 1);
+            mbar_init(pempty_bar(s), 1);      // the MMA commit
         }
         mbar_init(acc_bar, 1);
         *abort_flag = 0;
@@ -372,10 +391,10 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
         if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_pi) : "memory");
         const uint32_t bytes = args.nh * PI_BOX_BYTES;
         for (int it = 0; it < n_it; ++it) {
-            const int s = it % STAGES;
-            const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+            const int s = it % PSTAGES;
+            const uint32_t ph = (uint32_t)(it / PSTAGES) & 1u;
             bool ok = true;
-            if (it >= STAGES) ok = __all_sync(0xffffffffu, mbar_wait(empty_bar(s), ph ^ 1u, abort_flag));
+            if (it >= PSTAGES) ok = __all_sync(0xffffffffu, mbar_wait(pempty_bar(s), ph ^ 1u, abort_flag));
             if (!ok) {
                 if (lane == 0) {
                     *abort_flag = 1;
@@ -387,7 +406,7 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
                 mbar_arrive_expect_tx(pfull_bar(s), bytes);
                 const int t = (int)(rs + (int64_t)it * KS);
                 for (int h = 0; h < args.nh; ++h)
-                    tma_load_2d(mring + s * STAGE_BYTES + PI_OFF + h * PI_BOX_BYTES, &tm_pi, t, h * PI_BOX_ROWS,
+                    tma_load_2d(pring + s * PI_STAGE_BYTES + h * PI_BOX_BYTES, &tm_pi, t, h * PI_BOX_ROWS,
                                 pfull_bar(s));
             }
             __syncwarp();
@@ -398,9 +417,10 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
         const uint32_t id_last = idesc_tf32(TILE_M, args.n_last);
         bool ok = true;
         for (int it = 0; it < n_it; ++it) {
-            const int s = it % STAGES;
-            const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-            ok = __all_sync(0xffffffffu, mbar_wait(pfull_bar(s), ph, abort_flag) && mbar_wait(afull_bar(s), ph, abort_flag));
+            const int sp = it % PSTAGES, sa = it % ASTAGES;
+            const uint32_t pph = (uint32_t)(it / PSTAGES) & 1u, aph = (uint32_t)(it / ASTAGES) & 1u;
+            ok = __all_sync(0xffffffffu,
+                            mbar_wait(pfull_bar(sp), pph, abort_flag) && mbar_wait(afull_bar(sa), aph, abort_flag));
             if (!ok) {
                 if (lane == 0) {
                     *abort_flag = 1;
@@ -410,18 +430,19 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
             }
             tc_fence_after();
             if (lane == 0) {
-                const uint32_t sbase = mring + s * STAGE_BYTES;
+                const uint32_t abase = aring + sa * A_STAGE_BYTES, pbase = pring + sp * PI_STAGE_BYTES;
 #pragma unroll
                 for (int kb = 0; kb < KS / 8; ++kb) {
                     // both operands K-major, 64B swizzle: rows of 64 B, 8-row groups 512 B apart (SBO), K slice at +32 B
-                    const uint64_t ad = smem_desc(sbase + A_OFF + kb * 32, 16, 512, SWZ_64B);
+                    const uint64_t ad = smem_desc(abase + kb * 32, 16, 512, SWZ_64B);
                     for (int h = 0; h < args.nh; ++h) {
-                        const uint64_t bd = smem_desc(sbase + PI_OFF + h * PI_BOX_BYTES + kb * 32, 16, 512, SWZ_64B);
+                        const uint64_t bd = smem_desc(pbase + h * PI_BOX_BYTES + kb * 32, 16, 512, SWZ_64B);
                         mma_tf32(tmem + h * PI_BOX_ROWS, ad, bd, h == args.nh - 1 ? id_last : id_full,
                                  (it > 0 || kb > 0) ? 1u : 0u);
                     }
                 }
-                mma_commit(empty_bar(s));
+                mma_commit(aempty_bar(sa));
+                mma_commit(pempty_bar(sp));
             }
             __syncwarp();
         }
@@ -436,10 +457,10 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
         for (int it = 0; it < n_it; ++it) {
             const int d = it % DSTAGES;
             const uint32_t dph = (uint32_t)(it / DSTAGES) & 1u;
-            const int s = it % STAGES;
-            const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+            const int s = it % ASTAGES;
+            const uint32_t ph = (uint32_t)(it / ASTAGES) & 1u;
             bool ok = mbar_wait(dfull_bar(d), dph, abort_flag);
-            if (ok && it >= STAGES) ok = mbar_wait(empty_bar(s), ph ^ 1u, abort_flag);   // copy slot free
+            if (ok && it >= ASTAGES) ok = mbar_wait(aempty_bar(s), ph ^ 1u, abort_flag);   // copy slot free
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) {
                 if (lane == 0) {
@@ -459,7 +480,7 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
 #pragma unroll
             for (int t = 0; t < 8; t += 2) two_sum_square_x2(pack2(x[t], x[t + 1]), hi2, lo2);
             // K-major copy: data column m is row m (64 B = KS values); 64B swizzle puts chunk q at q ^ ((m >> 1) & 3)
-            float4* arow = (float4*)(base_ptr + DRING_BYTES + s * STAGE_BYTES + A_OFF + m * (KS * 4));
+            float4* arow = (float4*)(base_ptr + DRING_BYTES + s * A_STAGE_BYTES + m * (KS * 4));
             const int q0 = 2 * grp;
             arow[q0 ^ ((m >> 1) & 3)] = make_float4(to_tf32(x[0]), to_tf32(x[1]), to_tf32(x[2]), to_tf32(x[3]));
             arow[(q0 + 1) ^ ((m >> 1) & 3)] = make_float4(to_tf32(x[4]), to_tf32(x[5]), to_tf32(x[6]), to_tf32(x[7]));
