@@ -276,7 +276,8 @@ def main():
                 "peak_kind": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x %.0f MHz" % clk_mhz}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = sketch_traffic(sum(sk_rows) / len(sk_rows)) if tc_used else None
-    roof["kernel"] = "pi_gen_kernel + sketch_tc_kernel (tcgen05)" if tc_used else "sketch_simt_kernel"
+    roof["kernel"] = ("smp_sketch_accumulate: sketch_tc_kernel (tcgen05), Pi of the next block generated on a side "
+                      "stream meanwhile" if tc_used else "sketch_simt_kernel")
     roof["hbm_gbs"] = sk_bytes / sk_avg_s / 1e9
     roof["hbm_frac"] = roof["hbm_gbs"] / peaks["hbm_gbs"]
     roof["launch_ms"] = sk_avg_s * 1e3

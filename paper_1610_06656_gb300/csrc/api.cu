@@ -53,10 +53,11 @@ using namespace smp;
 namespace {
 
 void free_ctx(smp_ctx* c) {
+    release_tc(c);
     void* ptrs[] = {c->part,   c->nsq,    c->sk,      c->s_all,   c->D_all,   c->F,     c->row_ptr, c->col_ptr,
                     c->col,    c->qhat,   c->csc_row, c->csc_pos, c->alpha,   c->beta,  c->mask,    c->wpre,
                     c->erow,
-                    c->row_cnt, c->col_cnt, c->dev_err, c->tc_ws};
+                    c->row_cnt, c->col_cnt, c->dev_err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete c;
@@ -184,6 +185,7 @@ smp_status smp_sketch_reset(smp_ctx* c) {
     if (!c) return fail(nullptr, SMP_EINVAL, "null context");
     cudaError_t e = cudaMemsetAsync(c->part, 0, (size_t)c->splits * c->ntot * c->ldk * c->acc_bytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->nsq, 0, (size_t)c->splits * c->ntot * 8, c->stream);
+    if (e == cudaSuccess) e = tc_speculate_first_block(c);   // the next solve most likely starts at row 0
     if (e != cudaSuccess) return check_cuda(c, e, "smp_sketch_reset");
     c->finalized = false;
     c->sampled = false;

@@ -43,8 +43,17 @@ struct smp_ctx {
     int32_t* col_cnt = nullptr;     // [n2]
     int64_t mask_words = 0;
     int* dev_err = nullptr;         // device error word
-    void* tc_ws = nullptr;          // tensor-core engine workspace
-    size_t tc_ws_bytes = 0;
+    // tensor-core engine: two Pi buffers filled on a side stream; while one row block is sketched, Pi of the next
+    // one (row0 + nrows, same size) is generated speculatively into the other buffer
+    void* pi_buf[2] = {nullptr, nullptr};
+    size_t pi_buf_bytes = 0;
+    int64_t pi_row0[2] = {-1, -1};  // rows of Pi each buffer holds (or will hold once pi_ready fires)
+    int64_t pi_nrows[2] = {0, 0};
+    cudaStream_t gen_stream = nullptr;
+    cudaEvent_t pi_ready[2] = {nullptr, nullptr};   // recorded on gen_stream after a buffer's generation
+    cudaEvent_t pi_free[2] = {nullptr, nullptr};    // recorded on stream after the sketch that read a buffer
+    int pi_last = -1;                // buffer the last tensor-core sketch read
+    int64_t pi_last_rows = 0;        // largest row block sketched so far
     std::string err;
 };
 
@@ -73,6 +82,8 @@ cudaError_t launch_sketch_simt_into(int dtype, const void* A, int64_t lda, const
 
 // sketch_tc.cu
 bool tc_supported(const smp_ctx* c);
+void release_tc(smp_ctx* c);   // waits for the side stream, frees the Pi buffers, stream and events
+cudaError_t tc_speculate_first_block(smp_ctx* c);   // after a reset: Pi of rows [0, last block size) ahead of time
 bool tc_block_ok(const smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb);
 cudaError_t launch_sketch_tc(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t row0,
                              int64_t nrows);

@@ -61,6 +61,7 @@ constexpr int ARING_BYTES = ASTAGES * A_STAGE_BYTES;
 constexpr int PRING_BYTES = PSTAGES * PI_STAGE_BYTES;
 constexpr int SMEM_BYTES = DRING_BYTES + ARING_BYTES + PRING_BYTES + 1024 /* alignment */ + 256 /* barriers */;
 static_assert(SMEM_BYTES <= 232448, "shared memory budget");
+constexpr int PI_GEN_SMEM = 8192;  // see generate_pi
 constexpr int THREADS = 512;       // 16 warps: producers 0 and 2, MMA 1, copy warps on schedulers 0, 2, 3
 constexpr int NCOPY = 8;           // copy warps: (32-column box, 8-row group) pairs
 // copy warp c (0..7) is warp COPY_WARP[c]: warp ids 4, 6, 7, 8, 10, 11, 12, 14 live on schedulers 0, 2, 3 (id % 4),
@@ -584,7 +585,79 @@ bool make_map(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer, u
 
 bool aligned16(const void* p, int64_t ld) { return ((uintptr_t)p % 16 == 0) && (ld % 4 == 0); }
 
+// Pi buffers, side stream and events of the tensor-core engine (created on first use).
+cudaError_t ensure_pi_buffers(smp_ctx* c, size_t bytes) {
+    if (!c->gen_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->gen_stream, cudaStreamNonBlocking);
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = cudaEventCreateWithFlags(&c->pi_ready[b], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->pi_free[b], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    if (c->pi_buf_bytes >= bytes) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(c->gen_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // no sketch still reads the old buffers
+    if (e != cudaSuccess) return e;
+    for (int b = 0; b < 2; ++b) {
+        if (c->pi_buf[b]) cudaFree(c->pi_buf[b]);
+        c->pi_buf[b] = nullptr;
+        c->pi_row0[b] = -1;
+        c->pi_nrows[b] = 0;
+    }
+    c->pi_buf_bytes = 0;
+    for (int b = 0; b < 2; ++b) {
+        e = cudaMalloc(&c->pi_buf[b], bytes);
+        if (e != cudaSuccess) return e;
+    }
+    c->pi_buf_bytes = bytes;
+    return cudaSuccess;
+}
+
+// Pi for rows [row0, row0 + nrows) into buffer b on the side stream, once the last sketch that read b has ended.
+// The kernel asks for PI_GEN_SMEM bytes of shared memory it does not use: a sketch CTA leaves less than that free
+// on its SM, so the generator only runs on SMs the sketch grid leaves idle instead of slowing its CTAs down.
+cudaError_t generate_pi(smp_ctx* c, int b, int64_t row0, int64_t nrows, int k, int kpad, int64_t ld) {
+    cudaError_t e = cudaStreamWaitEvent(c->gen_stream, c->pi_free[b], 0);
+    if (e != cudaSuccess) return e;
+    const int64_t tpad = round_up(nrows, KS);
+    const dim3 g((unsigned)((tpad + 255) / 256), (unsigned)(kpad / 4));
+    pi_gen_kernel<<<smp::counted(g), 256, PI_GEN_SMEM, c->gen_stream>>>(
+        (float*)c->pi_buf[b], ld, k, kpad, row0, nrows, tpad, (uint32_t)c->p.seed, (uint32_t)(c->p.seed >> 32),
+        (float)(1.0 / std::sqrt((double)k)));
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(c->pi_ready[b], c->gen_stream);
+    if (e != cudaSuccess) return e;
+    c->pi_row0[b] = row0;
+    c->pi_nrows[b] = nrows;
+    return cudaSuccess;
+}
+
 }  // namespace
+
+cudaError_t tc_speculate_first_block(smp_ctx* c) {
+    if (!c->gen_stream || c->pi_last < 0 || c->pi_last_rows <= 0) return cudaSuccess;
+    const int other = 1 - c->pi_last;
+    if (c->pi_row0[other] == 0 && c->pi_nrows[other] >= c->pi_last_rows) return cudaSuccess;
+    const int k = c->p.k;
+    const int kmma = (int)round_up(k, 16);
+    const int nh = (kmma + PI_BOX_ROWS - 1) / PI_BOX_ROWS;
+    return generate_pi(c, other, 0, c->pi_last_rows, k, nh * PI_BOX_ROWS, round_up(c->max_rows, KS));
+}
+
+void release_tc(smp_ctx* c) {
+    if (c->gen_stream) cudaStreamSynchronize(c->gen_stream);
+    for (int b = 0; b < 2; ++b) {
+        if (c->pi_buf[b]) cudaFree(c->pi_buf[b]);
+        if (c->pi_ready[b]) cudaEventDestroy(c->pi_ready[b]);
+        if (c->pi_free[b]) cudaEventDestroy(c->pi_free[b]);
+        c->pi_buf[b] = nullptr;
+        c->pi_ready[b] = c->pi_free[b] = nullptr;
+    }
+    if (c->gen_stream) cudaStreamDestroy(c->gen_stream);
+    c->gen_stream = nullptr;
+    c->pi_buf_bytes = 0;
+}
 
 bool tc_supported(const smp_ctx* c) { return c->p.dtype == SMP_F32 && c->p.k <= MAX_KC && encode_fn() != nullptr; }
 
@@ -610,24 +683,23 @@ cudaError_t launch_sketch_tc_pi(smp_ctx* c, const void* A, int64_t lda, const vo
     const float* pi = Pi;
     int64_t pld = ldp;
     int64_t pi_rows = k;
+    int buf = -1;
     if (!pi) {
-        // generated Pi buffer: kpad rows (zero beyond k) x ld = round_up(max_rows, KS) columns
+        // generated Pi: kpad rows (zero beyond k) x ld = round_up(max_rows, KS) columns, double-buffered
         const int64_t ld = round_up(c->max_rows, KS);
         const int kpad = nh * PI_BOX_ROWS;
-        const size_t need = (size_t)kpad * ld * 4;
-        if (c->tc_ws_bytes < need) {
-            if (c->tc_ws) cudaFree(c->tc_ws);
-            c->tc_ws = nullptr;
-            c->tc_ws_bytes = 0;
-            cudaError_t e = cudaMalloc(&c->tc_ws, need);
+        cudaError_t e = ensure_pi_buffers(c, (size_t)kpad * ld * 4);
+        if (e != cudaSuccess) return e;
+        for (int b2 = 0; b2 < 2 && buf < 0; ++b2)
+            if (c->pi_row0[b2] == row0 && c->pi_nrows[b2] >= nrows) buf = b2;
+        if (buf < 0) {
+            buf = c->pi_row0[0] < 0 ? 0 : (c->pi_row0[1] < 0 ? 1 : (c->pi_nrows[0] <= c->pi_nrows[1] ? 0 : 1));
+            e = generate_pi(c, buf, row0, nrows, k, kpad, ld);
             if (e != cudaSuccess) return e;
-            c->tc_ws_bytes = need;
         }
-        const dim3 g((unsigned)((tpad + 255) / 256), (unsigned)(kpad / 4));
-        pi_gen_kernel<<<smp::counted(g), 256, 0, st>>>((float*)c->tc_ws, ld, k, kpad, row0, nrows, tpad,
-                                                       (uint32_t)c->p.seed, (uint32_t)(c->p.seed >> 32),
-                                                       (float)(1.0 / std::sqrt((double)k)));
-        pi = (const float*)c->tc_ws;
+        e = cudaStreamWaitEvent(st, c->pi_ready[buf], 0);
+        if (e != cudaSuccess) return e;
+        pi = (const float*)c->pi_buf[buf];
         pld = ld;
         pi_rows = kpad;
     }
@@ -665,7 +737,17 @@ cudaError_t launch_sketch_tc_pi(smp_ctx* c, const void* A, int64_t lda, const vo
     a.nsq = c->nsq;
     a.err = c->dev_err;
     sketch_tc_kernel<<<smp::counted(dim3((unsigned)tiles, (unsigned)splits)), THREADS, SMEM_BYTES, st>>>(ma, mb, mp, a);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || buf < 0) return e;
+    // the sketch reads buffer `buf` until it ends; meanwhile the other buffer gets Pi of the next row block
+    e = cudaEventRecord(c->pi_free[buf], st);
+    c->pi_last = buf;
+    c->pi_last_rows = std::max(c->pi_last_rows, nrows);
+    const int other = 1 - buf;
+    const int64_t next0 = row0 + nrows;
+    if (e == cudaSuccess && !(c->pi_row0[other] == next0 && c->pi_nrows[other] >= nrows))
+        e = generate_pi(c, other, next0, nrows, k, nh * PI_BOX_ROWS, round_up(c->max_rows, KS));
+    return e;
 }
 
 cudaError_t launch_sketch_tc(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t row0,
