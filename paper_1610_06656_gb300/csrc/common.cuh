@@ -139,6 +139,23 @@ __device__ __forceinline__ double rsqrt_refined(double d) {
     return y;
 }
 
+// 1/sqrt(d) for any positive normal binary64 d, with no out-of-range branch: d = m 4^h with m in [1, 4) (exact
+// exponent arithmetic), the binary32 estimate of 1/sqrt(m) refined by two Newton-Raphson steps as in rsqrt_refined,
+// then scaled by 2^-h (exact). Callers keep arrays in registers across it (no call to a division or square-root
+// routine).
+__device__ __forceinline__ double rsqrt_scaled(double d) {
+    const long long bits = __double_as_longlong(d);
+    const int h = (((int)((bits >> 52) & 0x7ff)) - 1023) >> 1;   // floor(exponent / 2)
+    const double m = __longlong_as_double(bits - ((long long)(2 * h) << 52));
+    float yf;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"((float)m));
+    double y = (double)yf;
+    const double hm = 0.5 * m;
+    y = y * fma(-hm * y, y, 1.5);
+    y = y * fma(-hm * y, y, 1.5);
+    return __longlong_as_double(__double_as_longlong(y) - ((long long)h << 52));
+}
+
 // Sum of 32 per-lane vectors: afterwards lane l holds sum over lanes of v[l]. Five butterfly rounds; in the round
 // with offset o each lane keeps the half of its live values selected by bit o of its lane id and adds the
 // partner's matching half (o shuffles per round, 31 in total).

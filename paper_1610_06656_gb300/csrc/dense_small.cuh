@@ -91,28 +91,15 @@ __global__ void chol_kernel(const double* __restrict__ G, int b, double* R, doub
     }
 }
 
-// Upper Cholesky factor of a b x b symmetric matrix (b <= 32) held in registers: lane i keeps row i of the matrix,
-// pivots and column entries travel by warp shuffles (right-looking elimination; the trailing updates of one column
-// are independent multiply-adds). Same pivot rule and output as chol_kernel. When nblk > 0, G is first formed as
-// the fixed-order sum of nblk partial Gram blocks part[blk][b * b] (the whole CTA reduces, warp 0 factors).
-__global__ void __launch_bounds__(256) chol32_kernel(const double* __restrict__ part, int nblk,
-                                                     const double* __restrict__ Gin, int b, double* R, double tol) {
-    __shared__ double Gs[32 * 32];
-    const double* G = Gin;
-    if (nblk > 0) {
-        const int npair = b * b;
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        for (int pq = warp; pq < npair; pq += (int)(blockDim.x >> 5)) {   // one warp per entry, as gram_reduce
-            double s = 0.0;
-            for (int k = lane; k < nblk; k += 32) s += part[(int64_t)k * npair + pq];
-            s = warp_sum(s);
-            if (lane == 0) Gs[pq] = s;
-        }
-        __syncthreads();
-        G = Gs;
-    }
-    if (threadIdx.x >= 32) return;
-    const int lane = threadIdx.x;
+// Upper Cholesky factor of a b x b symmetric matrix (b <= 32), same pivot rule and output as chol_kernel, on four
+// warps: every warp keeps the whole matrix in registers (lane i holds row i), computes each pivot and its column
+// (in parallel, identically), and updates only the trailing columns kk with kk % 4 == its warp id, so the binary64
+// work of the trailing updates is spread over the SM's four sub-partitions (on this part each issues about one
+// binary64 warp instruction per 64 cycles). Column j + 1 is then broadcast from the warp that updated it through
+// shared memory. Launch with 128 threads.
+__global__ void __launch_bounds__(128) chol32_kernel(const double* __restrict__ G, int b, double* R, double tol) {
+    __shared__ double col[2][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double a[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) a[k] = (lane < b && k < b) ? G[lane * b + k] : 0.0;
@@ -132,14 +119,19 @@ __global__ void __launch_bounds__(256) chol32_kernel(const double* __restrict__ 
             if (lane >= j) a[j] = lij;
 #pragma unroll
             for (int kk = j + 1; kk < 32; ++kk) {
-                if (kk < b) {
+                if (kk < b && (kk & 3) == w) {
                     const double lkj = __shfl_sync(0xffffffffu, lij, kk);   // L[kk][j]
                     if (lane > j) a[kk] = fma(-lij, lkj, a[kk]);
                 }
             }
+            if (j + 1 < b) {   // broadcast the next pivot column from the warp that updated it
+                if (((j + 1) & 3) == w) col[(j + 1) & 1][lane] = a[j + 1];
+                __syncthreads();
+                a[j + 1] = col[(j + 1) & 1][lane];
+            }
         }
     }
-    if (lane < b) {
+    if (w == 0 && lane < b) {
 #pragma unroll
         for (int k = 0; k < 32; ++k)
             if (k < b) R[k * b + lane] = k <= lane ? a[k] : 0.0;   // R = L^T

@@ -365,6 +365,133 @@ __global__ void __launch_bounds__(32) solve_kernel(const double* __restrict__ Gc
 #undef RI
 }
 
+// The same ridge + Cholesky solve with each row's system held in registers (r <= R: R (R + 1) / 2 + 2 R doubles).
+// Binary64 on this part issues about one warp instruction per 64 cycles per SM sub-partition whatever the number of
+// active lanes, so a warp's binary64 instruction count sets the time; registers remove the shared-memory round trip
+// the general kernel makes for every operand. Every index is a template constant (the loops are generated by
+// recursion, so no array is indexed at run time and nothing goes to local memory); r only enters warp-uniform guards.
+template <int R>
+struct RegChol {
+    __host__ __device__ static constexpr int T(int i) { return i * (i + 1) / 2; }   // row i of the packed triangle
+    // acc -= sum_{k < N} L[a + k] L[b + k]
+    template <int N, int A, int B>
+    static __device__ __forceinline__ void dot(const double (&L)[R * (R + 1) / 2], double& acc) {
+        if constexpr (N > 0) {
+            dot<N - 1, A, B>(L, acc);
+            acc = fma(-L[A + N - 1], L[B + N - 1], acc);
+        }
+    }
+    // rows I.. of column J below the pivot: L[I][J] = (L[I][J] - sum_k L[I][k] L[J][k]) / L[J][J]
+    template <int J, int I>
+    static __device__ __forceinline__ void below(double (&L)[R * (R + 1) / 2], double rj, int r) {
+        if constexpr (I < R) {
+            if (I < r) {
+                double v = L[T(I) + J];
+                dot<J, T(I), T(J)>(L, v);
+                L[T(I) + J] = v * rj;
+            }
+            below<J, I + 1>(L, rj, r);
+        }
+    }
+    template <int J>
+    static __device__ __forceinline__ void factor(double (&L)[R * (R + 1) / 2], double (&ri)[R], int r, bool& bad) {
+        if constexpr (J < R) {
+            if (J < r) {
+                double d = L[T(J) + J];
+                dot<J, T(J), T(J)>(L, d);
+                // a pivot that is not a positive normal number marks the system (2^-1022 is far below the ridge)
+                const bool ok = d >= 2.2250738585072014e-308 && d <= 1.7976931348623157e308;
+                bad = bad || !ok;
+                const double rj = ok ? rsqrt_scaled(d) : 0.0;
+                ri[J] = rj;
+                L[T(J) + J] = d * rj;
+                below<J, J + 1>(L, rj, r);
+            }
+            factor<J + 1>(L, ri, r, bad);
+        }
+    }
+    // y[I] = (y[I] - sum_{k < I} L[I][k] y[k]) ri[I], I = 0, 1, ...
+    template <int N, int A>
+    static __device__ __forceinline__ void doty(const double (&L)[R * (R + 1) / 2], const double (&y)[R], double& acc) {
+        if constexpr (N > 0) {
+            doty<N - 1, A>(L, y, acc);
+            acc = fma(-L[A + N - 1], y[N - 1], acc);
+        }
+    }
+    template <int I>
+    static __device__ __forceinline__ void forward(const double (&L)[R * (R + 1) / 2], const double (&ri)[R],
+                                                   double (&y)[R], int r) {
+        if constexpr (I < R) {
+            if (I < r) {
+                double v = y[I];
+                doty<I, T(I)>(L, y, v);
+                y[I] = v * ri[I];
+            }
+            forward<I + 1>(L, ri, y, r);
+        }
+    }
+    // y[I] = (y[I] - sum_{k > I, k < r} L[k][I] y[k]) ri[I], I = R - 1, ..., 0
+    template <int I, int K>
+    static __device__ __forceinline__ void colsum(const double (&L)[R * (R + 1) / 2], const double (&y)[R], int r,
+                                                  double& acc) {
+        if constexpr (K < R) {
+            if (K < r) acc = fma(-L[T(K) + I], y[K], acc);
+            colsum<I, K + 1>(L, y, r, acc);
+        }
+    }
+    template <int I>
+    static __device__ __forceinline__ void backward(const double (&L)[R * (R + 1) / 2], const double (&ri)[R],
+                                                    double (&y)[R], int r) {
+        if constexpr (I >= 0) {
+            if (I < r) {
+                double v = y[I];
+                colsum<I, I + 1>(L, y, r, v);
+                y[I] = v * ri[I];
+            }
+            backward<I - 1>(L, ri, y, r);
+        }
+    }
+};
+
+template <typename TF, int R>
+__global__ void __launch_bounds__(32) solve_reg_kernel(const double* __restrict__ Gc, int r, int64_t n_out, TF* Xout,
+                                                       int* err) {
+    using C = RegChol<R>;
+    const int64_t o = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    if (o >= n_out) return;
+    const int nt = r * (r + 1) / 2;
+    const double* src = Gc + o * (int64_t)(nt + r);
+    double L[R * (R + 1) / 2], y[R], ri[R];
+#pragma unroll
+    for (int e = 0; e < R * (R + 1) / 2; ++e) L[e] = e < nt ? src[e] : 0.0;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        y[i] = i < r ? src[nt + i] : 0.0;
+        ri[i] = 0.0;
+    }
+    double tr = 0.0;
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+        if (i < r) tr += L[C::T(i) + i];
+    const bool empty = !(tr > 0.0);
+    const double lam = 1e-10 * tr / (double)r;
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+        if (i < r) L[C::T(i) + i] += lam;
+    bool bad = false;   // not positive definite: the factorisation runs on, the row gets x = 0
+    C::template factor<0>(L, ri, r, bad);
+    if (empty || bad) {
+        if (bad && !empty) set_error(err, DEVERR_NUMERIC);
+        for (int i = 0; i < r; ++i) Xout[o * r + i] = TF(0);
+        return;
+    }
+    C::template forward<0>(L, ri, y, r);
+    C::template backward<R - 1>(L, ri, y, r);
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+        if (i < r) Xout[o * r + i] = (TF)y[i];
+}
+
 template <int RMAX>
 constexpr int solve_smem_bytes() {
     return (RMAX * (RMAX + 1) / 2 + 2 * RMAX) * 32 * 8;
@@ -474,7 +601,7 @@ void gram_chol(const TX* X, int64_t n, int b, double* part, double* G, double* R
     gram_partial_kernel<TX, TX><<<smp::counted(nblk), 256, 0, st>>>(X, X, n, b, b, part);
     gram_reduce_kernel<<<smp::counted(nblocks(b * b * 32, 256)), 256, 0, st>>>(part, nblk, b * b, G);
     if (b <= 32)
-        chol32_kernel<<<smp::counted(1), 32, 0, st>>>(nullptr, 0, G, b, R, 1e-28);
+        chol32_kernel<<<smp::counted(1), 128, 0, st>>>(G, b, R, 1e-28);
     else
         chol_kernel<<<smp::counted(1), 32, 0, st>>>(G, b, R, 1e-28);
 }
@@ -523,12 +650,15 @@ void launch_ls(int r, const Segments& sg, const int32_t* idx, const int64_t* pos
         seg_gram_kernel<TF, TG, TV, 8><<<smp::counted(g), 32 * LS_WARPS, 0, st>>>(sg.b, sg.e, sg.nseg, idx, pos,
                                                                                   vals, qhat, sub, sid, Fin, r, part);
         seg_reduce_kernel<TG><<<smp::counted(gr), 256, 0, st>>>(sg.start, part, r, n_out, Gc);
-        solve_kernel<TF, 8><<<smp::counted(gs), 32, solve_smem_bytes<8>(), st>>>(Gc, r, n_out, Xout, err);
+        solve_reg_kernel<TF, 12><<<smp::counted(gs), 32, 0, st>>>(Gc, r, n_out, Xout, err);
     } else if (r <= 16) {
         seg_gram_kernel<TF, TG, TV, 16><<<smp::counted(g), 32 * LS_WARPS, 0, st>>>(sg.b, sg.e, sg.nseg, idx, pos,
                                                                                    vals, qhat, sub, sid, Fin, r, part);
         seg_reduce_kernel<TG><<<smp::counted(gr), 256, 0, st>>>(sg.start, part, r, n_out, Gc);
-        solve_kernel<TF, 16><<<smp::counted(gs), 32, solve_smem_bytes<16>(), st>>>(Gc, r, n_out, Xout, err);
+        if (r <= 12)
+            solve_reg_kernel<TF, 12><<<smp::counted(gs), 32, 0, st>>>(Gc, r, n_out, Xout, err);
+        else
+            solve_kernel<TF, 16><<<smp::counted(gs), 32, solve_smem_bytes<16>(), st>>>(Gc, r, n_out, Xout, err);
     } else {
         seg_gram_kernel<TF, TG, TV, 32><<<smp::counted(g), 32 * LS_WARPS, 0, st>>>(sg.b, sg.e, sg.nseg, idx, pos,
                                                                                    vals, qhat, sub, sid, Fin, r, part);
