@@ -163,6 +163,51 @@ __global__ void __launch_bounds__(128) apply_rinv_kernel(const TIn* __restrict__
     for (int j = 0; j < b; ++j) Xout[i * b + j] = (TOut)x[j];
 }
 
+// apply_rinv_kernel for b <= 32 with the row in registers: the substitution is unrolled by template recursion (every
+// index of x is a compile-time constant, so x stays in registers instead of local memory); b only enters
+// warp-uniform guards. R^-1's diagonal comes from rsqrt_refined(d^2) as above.
+template <typename TC>
+struct Rinv32 {
+    template <int J, int L>
+    static __device__ __forceinline__ void dot(const TC* Rs, const TC (&x)[32], int b, TC& y) {
+        if constexpr (L < J) {
+            y -= x[L] * Rs[L * b + J];
+            dot<J, L + 1>(Rs, x, b, y);
+        }
+    }
+    template <int J, typename TIn>
+    static __device__ __forceinline__ void step(const TC* Rs, const TC* dinv, const TIn* xin, TC (&x)[32], int b) {
+        if constexpr (J < 32) {
+            if (J < b) {
+                TC y = (TC)xin[J];
+                dot<J, 0>(Rs, x, b, y);
+                x[J] = y * dinv[J];
+                step<J + 1>(Rs, dinv, xin, x, b);
+            }
+        }
+    }
+};
+
+template <typename TIn, typename TOut, typename TC>
+__global__ void __launch_bounds__(128) apply_rinv32_kernel(const TIn* __restrict__ Xin, int64_t n, int b,
+                                                           const double* __restrict__ R, TOut* Xout) {
+    __shared__ TC Rs[32 * 32];
+    __shared__ TC dinv[32];
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) Rs[e] = (TC)R[e];
+    for (int j = threadIdx.x; j < b; j += blockDim.x) {
+        const double d = R[j * b + j];
+        dinv[j] = d > 0.0 ? (TC)rsqrt_refined(d * d) : TC(0);
+    }
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    TC x[32];
+    Rinv32<TC>::template step<0>(Rs, dinv, Xin + i * b, x, b);
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+        if (j < b) Xout[i * b + j] = (TOut)x[j];
+}
+
 // Rotation (c, s) in the (p, q) plane that zeroes A_pq: theta = (A_qq - A_pp) / (2 A_pq),
 // t = sign(theta) / (|theta| + sqrt(theta^2 + 1)), c = 1 / sqrt(1 + t^2), s = t c. The binary64 version takes t
 // from binary32 arithmetic (the angle only steers convergence) and c from rsqrt_refined, so c^2 + s^2 = 1 to

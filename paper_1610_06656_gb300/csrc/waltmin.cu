@@ -606,13 +606,22 @@ void gram_chol(const TX* X, int64_t n, int b, double* part, double* G, double* R
         chol_kernel<<<smp::counted(1), 32, 0, st>>>(G, b, R, 1e-28);
 }
 
+// Xout = Xin R^-1 (registers for b <= 32).
+template <typename TIn, typename TOut, typename TC>
+void apply_rinv(const TIn* Xin, int64_t n, int b, const double* R, TOut* Xout, cudaStream_t st) {
+    if (b <= 32)
+        apply_rinv32_kernel<TIn, TOut, TC><<<smp::counted(nblocks(n, 128)), 128, 0, st>>>(Xin, n, b, R, Xout);
+    else
+        apply_rinv_kernel<TIn, TOut, TC><<<smp::counted(nblocks(n, 128)), 128, 0, st>>>(Xin, n, b, R, Xout);
+}
+
 template <typename TX, typename TQ, typename TC>
 void cholqr2(const TX* X, int64_t n, int b, TQ* Q, double* part, double* G, double* R1, double* R2, double* Rout,
              cudaStream_t st) {
     gram_chol<TX>(X, n, b, part, G, R1, st);
-    apply_rinv_kernel<TX, TQ, TC><<<smp::counted(nblocks(n, 128)), 128, 0, st>>>(X, n, b, R1, Q);
+    apply_rinv<TX, TQ, TC>(X, n, b, R1, Q, st);
     gram_chol<TQ>(Q, n, b, part, G, R2, st);
-    apply_rinv_kernel<TQ, TQ, TC><<<smp::counted(nblocks(n, 128)), 128, 0, st>>>(Q, n, b, R2, Q);
+    apply_rinv<TQ, TQ, TC>(Q, n, b, R2, Q, st);
     if (Rout) upper_mul_kernel<<<smp::counted(nblocks(b * b, 256)), 256, 0, st>>>(R2, R1, b, Rout);
 }
 
@@ -795,8 +804,15 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
         for (int it = 1; it <= max_iter; ++it) {
             spmm<TY>(cols_sg, c->csc_row, rv_csc, Y, n2, b, Yp, Z, st);   // Z = R^T Y
             spmm<TY>(rows_sg, c->col, rv, Z, n1, b, Yp, Yt, st);          // Y = R Z
+            const bool check = it % every == 0 || it == max_iter;
+            if (!check) {
+                // between checks one Cholesky-QR pass: the next product only needs a well-conditioned basis of the
+                // same span (orthogonality error ~ cond(Y) x unit roundoff); the checks orthonormalise twice
+                gram_chol<TY>(Yt, n1, b, part, G, R1, st);
+                apply_rinv<TY, TY, TY>(Yt, n1, b, R1, Y, st);
+                continue;
+            }
             cholqr2<TY, TY, TY>(Yt, n1, b, Y, part, G, R1, R2, nullptr, st);
-            if (it % every != 0 && it != max_iter) continue;
             spmm<TY>(cols_sg, c->csc_row, rv_csc, Y, n2, b, Yp, Z, st);   // C = Z^T Z, Z = R^T Y
             gram<TY, TY>(Z, Z, n2, b, b, part, G, st);
             bool done = false;
