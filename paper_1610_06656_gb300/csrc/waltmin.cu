@@ -643,10 +643,91 @@ void spmm(const Segments& sg, const int32_t* idx, const TY* val, const TY* X, in
     spmm_reduce_kernel<TY><<<smp::counted(nblocks(n_out * b, 256)), 256, 0, st>>>(sg.start, Yp, n_out, b, Y);
 }
 
+// ---------------------------------------------------------------------------------------------------------------
+// binary32 Gram path for r <= LANE_R: one sample per lane
+// ---------------------------------------------------------------------------------------------------------------
+constexpr int LANE_R = 12;
+constexpr int LANE_NT = LANE_R * (LANE_R + 1) / 2;
+constexpr int LANE_PS = (LANE_NT + LANE_R + 3) / 4 * 4;   // floats per segment partial (packed G, then b)
+
+// w_e = 1 / q^_e for every sample of Omega (binary32), once per WAltMin call.
+__global__ void weights_kernel(const double* __restrict__ qhat, int64_t nnz, float* wt) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nnz) return;
+    const double q = qhat[e];
+    wt[e] = q > 0.0 ? (float)(1.0 / q) : 0.f;
+}
+
+// Weighted Gram partials of one segment (<= 64 samples of one output row), one warp per segment, lane t taking
+// samples t, t + 32: every lane accumulates w f f^T (packed lower triangle, rows < r) and w m f of its own samples
+// in registers, then a butterfly transpose-sum over the lanes gives each value's segment total (fixed order).
+// Layout of a partial: LANE_PS floats, G(a, c) at a (a + 1) / 2 + c, b(a) at LANE_NT + a, zeros beyond r.
+template <typename TF, typename TV>
+__global__ void __launch_bounds__(32 * LS_WARPS) seg_gram_lane_kernel(
+    const int64_t* __restrict__ seg_b, const int64_t* __restrict__ seg_e, int64_t nseg,
+    const int32_t* __restrict__ idx, const int64_t* __restrict__ pos, const TV* __restrict__ vals,
+    const float* __restrict__ wt, const uint8_t* __restrict__ sub, int sid, const TF* __restrict__ Fin, int r,
+    float* part) {
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t s = (int64_t)blockIdx.x * LS_WARPS + wid;
+    if (s >= nseg) return;
+    float g[LANE_PS];
+#pragma unroll
+    for (int e = 0; e < LANE_PS; ++e) g[e] = 0.f;
+    const int64_t p1 = seg_e[s];
+    for (int64_t p = seg_b[s] + lane; p < p1; p += 32) {
+        const int64_t e = pos ? pos[p] : p;
+        if (sub != nullptr && sub[e] != sid) continue;
+        const float w = wt[e];
+        const float wm = w * (float)vals[e];
+        const TF* fr = Fin + (int64_t)idx[p] * r;
+        float f[LANE_R];
+#pragma unroll
+        for (int a = 0; a < LANE_R; ++a) f[a] = a < r ? (float)fr[a] : 0.f;
+#pragma unroll
+        for (int a = 0; a < LANE_R; ++a) {
+            if (a < r) {
+                const float wf = w * f[a];
+#pragma unroll
+                for (int c = 0; c <= a; ++c) g[a * (a + 1) / 2 + c] = fmaf(wf, f[c], g[a * (a + 1) / 2 + c]);
+                g[LANE_NT + a] = fmaf(wm, f[a], g[LANE_NT + a]);
+            }
+        }
+    }
+    float* dst = part + s * (int64_t)LANE_PS;
+#pragma unroll
+    for (int c0 = 0; c0 < LANE_PS; c0 += 32) {
+        float v[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = c0 + i < LANE_PS ? g[c0 + i] : 0.f;
+        const float tot = transpose_sum32(v, lane);
+        if (c0 + lane < LANE_PS) dst[c0 + lane] = tot;
+    }
+}
+
+// Gc[o] (binary64, the layout solve_reg_kernel reads: packed G of rows < r, then b) = sum of the row's segment
+// partials in segment order, in binary32. One warp per row, lanes over the partial's values.
+__global__ void __launch_bounds__(256) seg_reduce_lane_kernel(const int64_t* __restrict__ seg_start,
+                                                              const float* __restrict__ part, int r, int64_t n_out,
+                                                              double* Gc) {
+    const int64_t o = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (o >= n_out) return;
+    const int nt = r * (r + 1) / 2;
+    double* dst = Gc + o * (int64_t)(nt + r);
+    const int64_t s0 = seg_start[o], s1 = seg_start[o + 1];
+    for (int e = lane; e < LANE_PS; e += 32) {
+        float acc = 0.f;
+        for (int64_t s = s0; s < s1; ++s) acc += part[s * (int64_t)LANE_PS + e];
+        if (e < nt) dst[e] = (double)acc;
+        else if (e >= LANE_NT && e < LANE_NT + r) dst[nt + (e - LANE_NT)] = (double)acc;
+    }
+}
+
 template <typename TF, typename TG, typename TV>
 void launch_ls(int r, const Segments& sg, const int32_t* idx, const int64_t* pos, const TV* vals,
-               const double* qhat, const uint8_t* sub, int sid, const TF* Fin, int64_t n_out, TG* part, double* Gc,
-               TF* Xout, int* err, cudaStream_t st) {
+               const double* qhat, const float* wt, const uint8_t* sub, int sid, const TF* Fin, int64_t n_out,
+               TG* part, double* Gc, TF* Xout, int* err, cudaStream_t st) {
     const unsigned g = nblocks(sg.nseg, LS_WARPS);
     const unsigned gr = nblocks(n_out * 32, 256);
     const unsigned gs = nblocks(n_out, 32);
@@ -655,7 +736,12 @@ void launch_ls(int r, const Segments& sg, const int32_t* idx, const int64_t* pos
         cudaFuncSetAttribute(solve_kernel<TF, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, solve_smem_bytes<32>());
         attr = true;
     }
-    if (r <= 8) {
+    if (sizeof(TG) == 4 && r <= LANE_R) {
+        seg_gram_lane_kernel<TF, TV><<<smp::counted(g), 32 * LS_WARPS, 0, st>>>(sg.b, sg.e, sg.nseg, idx, pos, vals,
+                                                                                wt, sub, sid, Fin, r, (float*)part);
+        seg_reduce_lane_kernel<<<smp::counted(gr), 256, 0, st>>>(sg.start, (const float*)part, r, n_out, Gc);
+        solve_reg_kernel<TF, 12><<<smp::counted(gs), 32, 0, st>>>(Gc, r, n_out, Xout, err);
+    } else if (r <= 8) {
         seg_gram_kernel<TF, TG, TV, 8><<<smp::counted(g), 32 * LS_WARPS, 0, st>>>(sg.b, sg.e, sg.nseg, idx, pos,
                                                                                   vals, qhat, sub, sid, Fin, r, part);
         seg_reduce_kernel<TG><<<smp::counted(gr), 256, 0, st>>>(sg.start, part, r, n_out, Gc);
@@ -707,7 +793,8 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
     add(n1 + n2 + 2, 4);                     // segment counts
     add(n1 + n2 + 4, 8);                     // segment starts
     add(4 * nseg_max, 8);                    // segment begins / ends
-    add(nseg_max * (int64_t)(r * r + r), sizeof(TG));   // LS partials
+    add(nseg_max * (int64_t)std::max(r * r + r, LANE_PS), sizeof(TG));   // LS partials
+    add(nnz, 4);                                        // binary32 weights 1 / q^
     add(nseg_max * (int64_t)b, sizeof(TY));             // SpMM segment partials
     add(nmax * (int64_t)(r * (r + 1) / 2 + r), 8);      // compact per-row systems
     void* ws = nullptr;
@@ -744,7 +831,8 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
     rows_sg.start = ar.take<int64_t>(n1 + 1);
     cols_sg.start = ar.take<int64_t>(n2 + 1);
     int64_t* seg_be = ar.take<int64_t>(4 * nseg_max);
-    TG* lspart = ar.take<TG>(nseg_max * (int64_t)(r * r + r));
+    TG* lspart = ar.take<TG>(nseg_max * (int64_t)std::max(r * r + r, LANE_PS));
+    float* wt = ar.take<float>(nnz);
     TY* Yp = ar.take<TY>(nseg_max * (int64_t)b);
     double* Gc = ar.take<double>(nmax * (int64_t)(r * (r + 1) / 2 + r));
 
@@ -864,11 +952,13 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
         }
     }
     if (status == SMP_OK) {
+        if (nnz > 0)
+            weights_kernel<<<smp::counted(nblocks(nnz, 256)), 256, 0, st>>>(c->qhat, nnz, wt);
         for (int t = 0; t < T; ++t) {
-            launch_ls<TF, TG, TV>(r, cols_sg, c->csc_row, c->csc_pos, vals, c->qhat, subp, 2 * t + 1, Uf, n2, lspart,
-                                  Gc, Vf, c->dev_err, st);
-            launch_ls<TF, TG, TV>(r, rows_sg, c->col, nullptr, vals, c->qhat, subp, 2 * t + 2, Vf, n1, lspart, Gc,
-                                  Uf, c->dev_err, st);
+            launch_ls<TF, TG, TV>(r, cols_sg, c->csc_row, c->csc_pos, vals, c->qhat, wt, subp, 2 * t + 1, Uf, n2,
+                                  lspart, Gc, Vf, c->dev_err, st);
+            launch_ls<TF, TG, TV>(r, rows_sg, c->col, nullptr, vals, c->qhat, wt, subp, 2 * t + 2, Vf, n1, lspart,
+                                  Gc, Uf, c->dev_err, st);
         }
         if (T == 0) cudaMemsetAsync(Vf, 0, sizeof(TF) * n2 * r, st);
         // canonical form
