@@ -137,6 +137,19 @@ __global__ void ritz_kernel(const TY* __restrict__ Y, const double* __restrict__
     U0[e] = s;
 }
 
+// Rayleigh-Ritz rotation of the whole block: Yout = Y E (n1 x b times b x b), so the iteration continues in the
+// Ritz basis and the next check's b x b matrix is nearly diagonal (its Jacobi sweeps converge at once).
+template <typename TY>
+__global__ void rotate_kernel(const TY* __restrict__ Y, const double* __restrict__ E, int64_t n1, int b, TY* Yout) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n1 * b) return;
+    const int64_t i = e / b;
+    const int c = (int)(e - i * b);
+    TY s = TY(0);
+    for (int l = 0; l < b; ++l) s = fma(Y[i * b + l], (TY)E[l * b + c], s);
+    Yout[e] = s;
+}
+
 // Trim (step 6): zero row i when ||U0^i|| > 8 sqrt(r) ||A_i|| / ||A||_F.
 __global__ void trim_kernel(double* U0, int64_t n1, int r, const double* __restrict__ sA,
                             const double* __restrict__ F) {
@@ -943,6 +956,10 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
                 if (!dbl)   // Rayleigh-Ritz vectors from the binary32 eigenvectors of the last check
                     ritz_kernel<TY><<<smp::counted(nblocks(n1 * r, 256)), 256, 0, st>>>(Y, E, n1, b, r, U0);
                 break;
+            }
+            if (!dbl) {   // continue from the Ritz basis
+                rotate_kernel<TY><<<smp::counted(nblocks(n1 * b, 256)), 256, 0, st>>>(Y, E, n1, b, Yt);
+                std::swap(Y, Yt);
             }
         }
         if (status == SMP_OK) {
