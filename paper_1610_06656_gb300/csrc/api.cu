@@ -157,13 +157,16 @@ smp_status smp_sketch_accumulate(smp_ctx* c, const void* A, int64_t lda, const v
     smp_status s = check_block(c, A, lda, B, ldb, nrows);
     if (s != SMP_OK || nrows == 0) return s;
     if (row0 < 0) return fail(c, SMP_EINVAL, "row0 < 0");
-    const bool tc_ok = tc_block_ok(c, A, lda, B, ldb);
+    const bool bf16 = c->p.dtype == SMP_BF16;
+    const bool tc_ok = bf16 ? bf16_block_ok(c, A, lda, B, ldb) : tc_block_ok(c, A, lda, B, ldb);
     if (c->p.engine == SMP_ENGINE_TC && !tc_ok)
         return fail(c, SMP_EUNSUPPORTED,
-                    "the tensor-core sketch needs SMP_F32, k <= 512, 16-byte aligned blocks and lda, ldb % 4 == 0");
+                    "the tensor-core sketch needs SMP_F32 with k <= 512 and lda, ldb % 4 == 0, or SMP_BF16 with "
+                    "k <= 1024 and lda, ldb % 8 == 0, and 16-byte aligned blocks");
     const bool want_tc = c->p.engine == SMP_ENGINE_TC || (c->p.engine == SMP_ENGINE_AUTO && tc_ok);
-    cudaError_t e = want_tc ? launch_sketch_tc(c, A, lda, B, ldb, row0, nrows)
-                            : launch_sketch_simt(c, A, lda, B, ldb, row0, nrows, nullptr, 0);
+    cudaError_t e = !want_tc ? launch_sketch_simt(c, A, lda, B, ldb, row0, nrows, nullptr, 0)
+                             : bf16 ? launch_sketch_bf16(c, A, lda, B, ldb, row0, nrows, nullptr, 0)
+                                    : launch_sketch_tc(c, A, lda, B, ldb, row0, nrows);
     return check_cuda(c, e, "smp_sketch_accumulate");
 }
 
@@ -172,11 +175,15 @@ smp_status smp_sketch_accumulate_pi(smp_ctx* c, const void* Pi, int64_t ldp, con
     smp_status s = check_block(c, A, lda, B, ldb, nrows);
     if (s != SMP_OK || nrows == 0) return s;
     if (!Pi || ldp < nrows) return fail(c, SMP_EINVAL, "Pi_blk is null or ldp < nrows");
-    const bool tc_ok = tc_block_ok(c, A, lda, B, ldb) && ((uintptr_t)Pi % 16 == 0) && (ldp % 4 == 0);
+    const bool bf16 = c->p.dtype == SMP_BF16;
+    const bool tc_ok = bf16 ? bf16_block_ok(c, A, lda, B, ldb)
+                            : tc_block_ok(c, A, lda, B, ldb) && ((uintptr_t)Pi % 16 == 0) && (ldp % 4 == 0);
     if (c->p.engine == SMP_ENGINE_TC && !tc_ok)
         return fail(c, SMP_EUNSUPPORTED, "the tensor-core sketch needs 16-byte aligned Pi and ldp % 4 == 0");
     if (c->p.engine == SMP_ENGINE_TC || (c->p.engine == SMP_ENGINE_AUTO && tc_ok))
-        return check_cuda(c, launch_sketch_tc_pi(c, A, lda, B, ldb, row0, nrows, (const float*)Pi, ldp),
+        return check_cuda(c,
+                          bf16 ? launch_sketch_bf16(c, A, lda, B, ldb, row0, nrows, (const float*)Pi, ldp)
+                               : launch_sketch_tc_pi(c, A, lda, B, ldb, row0, nrows, (const float*)Pi, ldp),
                           "smp_sketch_accumulate_pi");
     return check_cuda(c, launch_sketch_simt(c, A, lda, B, ldb, row0, nrows, Pi, ldp), "smp_sketch_accumulate_pi");
 }

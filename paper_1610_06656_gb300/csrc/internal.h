@@ -84,6 +84,29 @@ cudaError_t launch_sketch_simt_into(int dtype, const void* A, int64_t lda, const
 bool tc_supported(const smp_ctx* c);
 void release_tc(smp_ctx* c);   // waits for the side stream, frees the Pi buffers, stream and events
 cudaError_t tc_speculate_first_block(smp_ctx* c);   // after a reset: Pi of rows [0, last block size) ahead of time
+// Generated Pi of the tensor-core engines: kpad rows (a multiple of 256, zero beyond k) x ld columns (row stride),
+// esize bytes per element (4: TF32 in binary32 containers, 2: BF16).
+struct PiGeom {
+    int kpad;
+    int64_t ld;
+    int esize;
+};
+PiGeom pi_geom(const smp_ctx* c);
+// Buffer holding Pi of rows [row0, row0 + nrows) (generated now on the side stream if no buffer has it); the
+// context's stream waits for it.
+cudaError_t pi_acquire(smp_ctx* c, int64_t row0, int64_t nrows, int* buf);
+// After the sketch that reads buffer b is enqueued: mark b free at its end and generate Pi of the next row block
+// into the other buffer.
+cudaError_t pi_release(smp_ctx* c, int b, int64_t row0, int64_t nrows);
+// A caller's Pi (k x nrows binary32, row stride ldp) rounded into a Pi buffer (BF16 contexts); the buffer is then
+// released with pi_release like a generated one.
+cudaError_t pi_import(smp_ctx* c, const float* Pi, int64_t ldp, int64_t nrows, int* buf);
+
+// sketch_bf16.cu
+bool bf16_tc_supported(const smp_ctx* c);
+bool bf16_block_ok(const smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb);
+cudaError_t launch_sketch_bf16(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t row0,
+                               int64_t nrows, const float* Pi, int64_t ldp);
 bool tc_block_ok(const smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb);
 cudaError_t launch_sketch_tc(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t row0,
                              int64_t nrows);

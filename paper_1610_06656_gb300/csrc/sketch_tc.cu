@@ -26,9 +26,11 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "tc_common.cuh"
 
 namespace smp {
 namespace {
+using namespace tc;
 
 constexpr int TILE_M = 128;        // data columns per CTA (MMA M)
 constexpr int KS = 16;             // data rows per pipeline stage (two K = 8 MMA slices)
@@ -62,6 +64,7 @@ constexpr int PRING_BYTES = PSTAGES * PI_STAGE_BYTES;
 constexpr int SMEM_BYTES = DRING_BYTES + ARING_BYTES + PRING_BYTES + 1024 /* alignment */ + 256 /* barriers */;
 static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 constexpr int PI_GEN_SMEM = 8192;  // see generate_pi
+constexpr int PI_ROW_PAD = 32;     // Pi buffers: rows padded to a multiple of 32 (both engines' stage heights)
 constexpr int THREADS = 512;       // 16 warps: producers 0 and 2, MMA 1, copy warps on schedulers 0, 2, 3
 constexpr int NCOPY = 8;           // copy warps: (32-column box, 8-row group) pairs
 // copy warp c (0..7) is warp COPY_WARP[c]: warp ids 4, 6, 7, 8, 10, 11, 12, 14 live on schedulers 0, 2, 3 (id % 4),
@@ -79,166 +82,6 @@ __device__ __forceinline__ int copy_index(int warp) {
         default: return -1;
     }
 }
-constexpr unsigned long long WAIT_NS = 2000000000ull;       // 2 s: far beyond any legitimate wait
-
-// ------------------------------------------------------------------------------------------------ PTX wrappers
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long global_timer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-// One bounded try_wait: the thread may sleep in the hardware until the phase completes or SUSPEND_NS pass (a
-// polling loop without the hint spends issue slots and shared-memory cycles the copy warps and the MMA need).
-constexpr uint32_t SUSPEND_NS = 20000;
-__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity), "r"(SUSPEND_NS)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait on an mbarrier phase; false after WAIT_NS (the caller records the timeout and unwinds).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-    if (mbar_test(bar, parity)) return true;
-    const unsigned long long t0 = global_timer();
-    for (;;) {
-        if (mbar_test(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (global_timer() - t0 > WAIT_NS) return false;
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-        "[%4];" ::"r"(dst),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-// 32 consecutive TMEM columns of this warp's 32 lanes (lane i of the warp <- TMEM lane base + i).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Shared-memory matrix descriptor (tcgen05): start >> 4 in bits 0-13, leading-dimension byte offset >> 4 in 16-29,
-// stride-dimension byte offset >> 4 in 32-45, descriptor version 1 in bits 46-47, swizzle mode in bits 61-63.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t swizzle) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)swizzle << 61;
-    return d;
-}
-constexpr uint32_t SWZ_128B = 2, SWZ_64B = 4;
-
-// Instruction descriptor, kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32 (bits 7-9, 10-12 = 2), both K-major
-// (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-
-// Packed binary32 pairs (f32x2: two independent IEEE round-to-nearest lanes per instruction).
-__device__ __forceinline__ uint64_t pack2(float a, float b) {
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void unpack2(uint64_t r, float& a, float& b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-}
-__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
-    uint64_t d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
-    uint64_t d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
-    uint64_t d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
-    uint64_t d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-
-// Compensated accumulation of x^2 into (hi, lo), on two independent accumulators at once (lane by lane): the
-// product's rounding error comes from an FMA, the sum's from TwoSum (Knuth), and both are folded into lo.
-__device__ __forceinline__ void two_sum_square_x2(uint64_t x, uint64_t& hi, uint64_t& lo) {
-    const uint64_t p = mul2(x, x);
-    const uint64_t e = fma2(x, x, p ^ 0x8000000080000000ull);   // x*x - p exactly (sign flip of both lanes)
-    const uint64_t s2 = add2(hi, p);
-    const uint64_t bp = sub2(s2, hi);
-    const uint64_t err = add2(sub2(hi, sub2(s2, bp)), sub2(p, bp));
-    hi = s2;
-    lo = add2(lo, add2(err, e));
-}
-
 // ------------------------------------------------------------------------------------------------ Pi generation
 __device__ __forceinline__ float to_tf32(float x) {
     uint32_t y;
@@ -246,9 +89,14 @@ __device__ __forceinline__ float to_tf32(float x) {
     return __uint_as_float(y);
 }
 
-// pi[a][t] (ld = ldp) = Pi(a, row0 + t) rounded to TF32 for a < k, t < nrows; 0 for k <= a < kpad or
-// nrows <= t < tpad. One thread per (t, group of four sketch rows): one Philox block feeds four rows.
-__global__ void __launch_bounds__(256) pi_gen_kernel(float* __restrict__ pi, int64_t ldp, int k, int kpad,
+__device__ __forceinline__ void store_pi(float* p, float z) { *p = to_tf32(z); }
+__device__ __forceinline__ void store_pi(__nv_bfloat16* p, float z) { *p = __float2bfloat16_rn(z); }
+
+// pi[a][t] (ld = ldp) = Pi(a, row0 + t) rounded to the operand type (TF32 in a binary32 container, or BF16) for
+// a < k, t < nrows; 0 for k <= a < kpad or nrows <= t < tpad. One thread per (t, group of four sketch rows): one
+// Philox block feeds four rows.
+template <typename TP>
+__global__ void __launch_bounds__(256) pi_gen_kernel(TP* __restrict__ pi, int64_t ldp, int k, int kpad,
                                                      int64_t row0, int64_t nrows, int64_t tpad, uint32_t k0,
                                                      uint32_t k1, float scale) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -261,11 +109,11 @@ __global__ void __launch_bounds__(256) pi_gen_kernel(float* __restrict__ pi, int
         box_muller_f32(x.x, x.y, z[0], z[1]);
         box_muller_f32(x.z, x.w, z[2], z[3]);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) z[q] = (4 * g + q < k) ? to_tf32(z[q] * scale) : 0.f;
+        for (int q = 0; q < 4; ++q) z[q] = (4 * g + q < k) ? z[q] * scale : 0.f;
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-        if (4 * g + q < kpad) pi[(int64_t)(4 * g + q) * ldp + t] = z[q];
+        if (4 * g + q < kpad) store_pi(pi + (int64_t)(4 * g + q) * ldp + t, z[q]);
 }
 
 // ------------------------------------------------------------------------------------------------ main kernel
@@ -551,38 +399,6 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
 }
 
 // ------------------------------------------------------------------------------------------------ host side
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)p;
-    });
-    return fn;
-}
-
-// 2-D fp32 tensor map: inner extent `inner` (contiguous), `outer` rows of `ld` floats, box {box_inner, box_outer}.
-bool make_map(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer, uint64_t ld, uint32_t box_inner,
-              uint32_t box_outer, CUtensorMapSwizzle swz) {
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) return false;
-    const cuuint64_t dims[2] = {inner, outer};
-    const cuuint64_t strides[1] = {ld * 4};
-    const cuuint32_t box[2] = {box_inner, box_outer};
-    const cuuint32_t estr[2] = {1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 bool aligned16(const void* p, int64_t ld) { return ((uintptr_t)p % 16 == 0) && (ld % 4 == 0); }
 
 // Pi buffers, side stream and events of the tensor-core engine (created on first use).
@@ -617,14 +433,21 @@ cudaError_t ensure_pi_buffers(smp_ctx* c, size_t bytes) {
 // Pi for rows [row0, row0 + nrows) into buffer b on the side stream, once the last sketch that read b has ended.
 // The kernel asks for PI_GEN_SMEM bytes of shared memory it does not use: a sketch CTA leaves less than that free
 // on its SM, so the generator only runs on SMs the sketch grid leaves idle instead of slowing its CTAs down.
-cudaError_t generate_pi(smp_ctx* c, int b, int64_t row0, int64_t nrows, int k, int kpad, int64_t ld) {
+cudaError_t generate_pi(smp_ctx* c, int b, int64_t row0, int64_t nrows) {
     cudaError_t e = cudaStreamWaitEvent(c->gen_stream, c->pi_free[b], 0);
     if (e != cudaSuccess) return e;
-    const int64_t tpad = round_up(nrows, KS);
-    const dim3 g((unsigned)((tpad + 255) / 256), (unsigned)(kpad / 4));
-    pi_gen_kernel<<<smp::counted(g), 256, PI_GEN_SMEM, c->gen_stream>>>(
-        (float*)c->pi_buf[b], ld, k, kpad, row0, nrows, tpad, (uint32_t)c->p.seed, (uint32_t)(c->p.seed >> 32),
-        (float)(1.0 / std::sqrt((double)k)));
+    const PiGeom gm = pi_geom(c);
+    const int k = c->p.k;
+    const int64_t tpad = round_up(nrows, PI_ROW_PAD);
+    const dim3 g((unsigned)((tpad + 255) / 256), (unsigned)(gm.kpad / 4));
+    const uint32_t k0 = (uint32_t)c->p.seed, k1 = (uint32_t)(c->p.seed >> 32);
+    const float scale = (float)(1.0 / std::sqrt((double)k));
+    if (gm.esize == 2)
+        pi_gen_kernel<__nv_bfloat16><<<smp::counted(g), 256, PI_GEN_SMEM, c->gen_stream>>>(
+            (__nv_bfloat16*)c->pi_buf[b], gm.ld, k, gm.kpad, row0, nrows, tpad, k0, k1, scale);
+    else
+        pi_gen_kernel<float><<<smp::counted(g), 256, PI_GEN_SMEM, c->gen_stream>>>(
+            (float*)c->pi_buf[b], gm.ld, k, gm.kpad, row0, nrows, tpad, k0, k1, scale);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaEventRecord(c->pi_ready[b], c->gen_stream);
     if (e != cudaSuccess) return e;
@@ -635,14 +458,78 @@ cudaError_t generate_pi(smp_ctx* c, int b, int64_t row0, int64_t nrows, int k, i
 
 }  // namespace
 
+PiGeom pi_geom(const smp_ctx* c) {
+    PiGeom g;
+    g.kpad = (int)round_up(round_up(c->p.k, 16), 256);
+    g.ld = round_up(c->max_rows, PI_ROW_PAD);
+    g.esize = c->p.dtype == SMP_BF16 ? 2 : 4;
+    return g;
+}
+
+cudaError_t pi_acquire(smp_ctx* c, int64_t row0, int64_t nrows, int* buf) {
+    const PiGeom gm = pi_geom(c);
+    cudaError_t e = ensure_pi_buffers(c, (size_t)gm.kpad * gm.ld * gm.esize);
+    if (e != cudaSuccess) return e;
+    int b = -1;
+    for (int b2 = 0; b2 < 2 && b < 0; ++b2)
+        if (c->pi_row0[b2] == row0 && c->pi_nrows[b2] >= nrows) b = b2;
+    if (b < 0) {
+        b = c->pi_row0[0] < 0 ? 0 : (c->pi_row0[1] < 0 ? 1 : (c->pi_nrows[0] <= c->pi_nrows[1] ? 0 : 1));
+        e = generate_pi(c, b, row0, nrows);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaStreamWaitEvent(c->stream, c->pi_ready[b], 0);
+    *buf = b;
+    return e;
+}
+
+cudaError_t pi_release(smp_ctx* c, int b, int64_t row0, int64_t nrows) {
+    cudaError_t e = cudaEventRecord(c->pi_free[b], c->stream);
+    c->pi_last = b;
+    c->pi_last_rows = std::max(c->pi_last_rows, nrows);
+    const int other = 1 - b;
+    const int64_t next0 = row0 + nrows;
+    if (e == cudaSuccess && !(c->pi_row0[other] == next0 && c->pi_nrows[other] >= nrows))
+        e = generate_pi(c, other, next0, nrows);
+    return e;
+}
+
+namespace {
+// dst[a][t] (ld) = src[a][t] (ldp) rounded to BF16 for a < k, t < nrows; zeros elsewhere up to kpad x tpad.
+__global__ void pi_import_bf16_kernel(const float* __restrict__ src, int64_t ldp, int k, int64_t nrows,
+                                      __nv_bfloat16* dst, int64_t ld, int kpad, int64_t tpad) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int a = blockIdx.y;
+    if (t >= tpad || a >= kpad) return;
+    const float v = (a < k && t < nrows) ? src[(int64_t)a * ldp + t] : 0.f;
+    dst[(int64_t)a * ld + t] = __float2bfloat16_rn(v);
+}
+}  // namespace
+
+cudaError_t pi_import(smp_ctx* c, const float* Pi, int64_t ldp, int64_t nrows, int* buf) {
+    const PiGeom gm = pi_geom(c);
+    cudaError_t e = ensure_pi_buffers(c, (size_t)gm.kpad * gm.ld * gm.esize);
+    if (e != cudaSuccess) return e;
+    const int b = c->pi_last < 0 ? 0 : 1 - c->pi_last;
+    // the caller's Pi replaces whatever the buffer held; the stream waits for the buffer's generator and readers
+    e = cudaStreamWaitEvent(c->stream, c->pi_ready[b], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->pi_free[b], 0);
+    if (e != cudaSuccess) return e;
+    c->pi_row0[b] = -1;
+    c->pi_nrows[b] = 0;
+    const int64_t tpad = round_up(nrows, PI_ROW_PAD);
+    if (gm.esize != 2) return cudaErrorInvalidValue;
+    pi_import_bf16_kernel<<<smp::counted(dim3((unsigned)((tpad + 255) / 256), (unsigned)gm.kpad)), 256, 0,
+                            c->stream>>>(Pi, ldp, c->p.k, nrows, (__nv_bfloat16*)c->pi_buf[b], gm.ld, gm.kpad, tpad);
+    *buf = b;
+    return cudaGetLastError();
+}
+
 cudaError_t tc_speculate_first_block(smp_ctx* c) {
     if (!c->gen_stream || c->pi_last < 0 || c->pi_last_rows <= 0) return cudaSuccess;
     const int other = 1 - c->pi_last;
     if (c->pi_row0[other] == 0 && c->pi_nrows[other] >= c->pi_last_rows) return cudaSuccess;
-    const int k = c->p.k;
-    const int kmma = (int)round_up(k, 16);
-    const int nh = (kmma + PI_BOX_ROWS - 1) / PI_BOX_ROWS;
-    return generate_pi(c, other, 0, c->pi_last_rows, k, nh * PI_BOX_ROWS, round_up(c->max_rows, KS));
+    return generate_pi(c, other, 0, c->pi_last_rows);
 }
 
 void release_tc(smp_ctx* c) {
@@ -685,23 +572,13 @@ cudaError_t launch_sketch_tc_pi(smp_ctx* c, const void* A, int64_t lda, const vo
     int64_t pi_rows = k;
     int buf = -1;
     if (!pi) {
-        // generated Pi: kpad rows (zero beyond k) x ld = round_up(max_rows, KS) columns, double-buffered
-        const int64_t ld = round_up(c->max_rows, KS);
-        const int kpad = nh * PI_BOX_ROWS;
-        cudaError_t e = ensure_pi_buffers(c, (size_t)kpad * ld * 4);
+        // generated Pi: kpad rows (zero beyond k), double-buffered and generated one block ahead on a side stream
+        cudaError_t e = pi_acquire(c, row0, nrows, &buf);
         if (e != cudaSuccess) return e;
-        for (int b2 = 0; b2 < 2 && buf < 0; ++b2)
-            if (c->pi_row0[b2] == row0 && c->pi_nrows[b2] >= nrows) buf = b2;
-        if (buf < 0) {
-            buf = c->pi_row0[0] < 0 ? 0 : (c->pi_row0[1] < 0 ? 1 : (c->pi_nrows[0] <= c->pi_nrows[1] ? 0 : 1));
-            e = generate_pi(c, buf, row0, nrows, k, kpad, ld);
-            if (e != cudaSuccess) return e;
-        }
-        e = cudaStreamWaitEvent(st, c->pi_ready[buf], 0);
-        if (e != cudaSuccess) return e;
+        const PiGeom gm = pi_geom(c);
         pi = (const float*)c->pi_buf[buf];
-        pld = ld;
-        pi_rows = kpad;
+        pld = gm.ld;
+        pi_rows = gm.kpad;
     }
     CUtensorMap ma, mb, mp;
     const void* Bp = c->p.same_ab ? A : B;
@@ -740,14 +617,7 @@ cudaError_t launch_sketch_tc_pi(smp_ctx* c, const void* A, int64_t lda, const vo
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || buf < 0) return e;
     // the sketch reads buffer `buf` until it ends; meanwhile the other buffer gets Pi of the next row block
-    e = cudaEventRecord(c->pi_free[buf], st);
-    c->pi_last = buf;
-    c->pi_last_rows = std::max(c->pi_last_rows, nrows);
-    const int other = 1 - buf;
-    const int64_t next0 = row0 + nrows;
-    if (e == cudaSuccess && !(c->pi_row0[other] == next0 && c->pi_nrows[other] >= nrows))
-        e = generate_pi(c, other, next0, nrows, k, nh * PI_BOX_ROWS, round_up(c->max_rows, KS));
-    return e;
+    return pi_release(c, buf, row0, nrows);
 }
 
 cudaError_t launch_sketch_tc(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t row0,
