@@ -53,8 +53,9 @@ typedef enum {
 typedef enum {
     SMP_ENGINE_AUTO = 0,   /* tensor-core sketch where the dtype has one, else SIMT */
     SMP_ENGINE_SIMT = 1,   /* CUDA-core sketch: FP32 FMA (FP64 for SMP_F64); the exact-arithmetic reference */
-    SMP_ENGINE_TC = 2      /* tcgen05 sketch (TF32 operands, FP32 accumulation) for SMP_F32 with k <= 512;
-                              row blocks must be 16-byte aligned with lda, ldb multiples of 4 */
+    SMP_ENGINE_TC = 2      /* tcgen05 sketch, FP32 accumulation: SMP_F32 as TF32 operands with k <= 512 (row
+                              blocks 16-byte aligned, lda, ldb multiples of 4); SMP_BF16 as BF16 operands with
+                              k <= 1024 (row blocks 16-byte aligned, lda, ldb multiples of 8) */
 } smp_engine;
 
 /* smp_waltmin flags */
@@ -95,8 +96,9 @@ smp_status smp_sketch_accumulate(smp_ctx* ctx, const void* A_blk_dev, int64_t ld
 
 /* Same as smp_sketch_accumulate but with Pi[:, row0:row0+nrows] supplied by the caller (test hook: Pi = I, or
  * the oracle's Pi). Pi_blk_dev is k x nrows row-major with leading dimension ldp, element type float (double for
- * SMP_F64). Runs the context's engine; the tensor-core engine reads Pi through TMA and needs a 16-byte aligned
- * Pi_blk_dev and ldp % 4 == 0 (SMP_ENGINE_AUTO falls back to the SIMT engine otherwise). */
+ * SMP_F64). Runs the context's engine; the SMP_F32 tensor-core engine reads Pi through TMA and needs a 16-byte
+ * aligned Pi_blk_dev and ldp % 4 == 0 (SMP_ENGINE_AUTO falls back to the SIMT engine otherwise); the SMP_BF16 one
+ * rounds Pi to BF16 into its own buffer first. */
 smp_status smp_sketch_accumulate_pi(smp_ctx* ctx, const void* Pi_blk_dev, int64_t ldp, const void* A_blk_dev,
                                     int64_t lda, const void* B_blk_dev, int64_t ldb, int64_t row0, int64_t nrows);
 
