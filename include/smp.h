@@ -53,9 +53,13 @@ typedef enum {
 typedef enum {
     SMP_ENGINE_AUTO = 0,   /* tensor-core sketch where the dtype has one, else SIMT */
     SMP_ENGINE_SIMT = 1,   /* CUDA-core sketch: FP32 FMA (FP64 for SMP_F64); the exact-arithmetic reference */
-    SMP_ENGINE_TC = 2      /* tcgen05 sketch, FP32 accumulation: SMP_F32 as TF32 operands with k <= 512 (row
+    SMP_ENGINE_TC = 2,     /* tcgen05 sketch, FP32 accumulation: SMP_F32 as TF32 operands with k <= 512 (row
                               blocks 16-byte aligned, lda, ldb multiples of 4); SMP_BF16 as BF16 operands with
                               k <= 1024 (row blocks 16-byte aligned, lda, ldb multiples of 8) */
+    SMP_ENGINE_TC_FP8 = 3  /* tcgen05 sketch of SMP_BF16 row blocks with FP8 E4M3 operands: each block is scaled by
+                              one power of two per matrix, 2^ceil(log2(max |x| / 448)), Pi is E4M3 of the normals,
+                              FP32 accumulation; column norms of the stored BF16 values. k <= 1024, alignment as for
+                              SMP_BF16. Never chosen by SMP_ENGINE_AUTO. */
 } smp_engine;
 
 /* smp_waltmin flags */

@@ -96,7 +96,9 @@ smp_status smp_sketch_begin(const smp_params* params, void* stream, smp_ctx** ou
         return fail(nullptr, SMP_EINVAL, "n1, n2 must be in [1, 2^30]");
     if (p.same_ab && p.n1 != p.n2) return fail(nullptr, SMP_EINVAL, "same_ab needs n1 == n2");
     if (p.k < 1 || p.k > 1024) return fail(nullptr, SMP_EINVAL, "k must be in [1, 1024]");
-    if (p.engine < SMP_ENGINE_AUTO || p.engine > SMP_ENGINE_TC) return fail(nullptr, SMP_EINVAL, "unknown engine");
+    if (p.engine < SMP_ENGINE_AUTO || p.engine > SMP_ENGINE_TC_FP8) return fail(nullptr, SMP_EINVAL, "unknown engine");
+    if (p.engine == SMP_ENGINE_TC_FP8 && p.dtype != SMP_BF16)
+        return fail(nullptr, SMP_EUNSUPPORTED, "SMP_ENGINE_TC_FP8 takes SMP_BF16 row blocks");
     if (p.max_rows < 0) return fail(nullptr, SMP_EINVAL, "max_rows < 0");
     smp_ctx* c = new (std::nothrow) smp_ctx();
     if (!c) return fail(nullptr, SMP_ENOMEM, "host allocation");
@@ -157,6 +159,11 @@ smp_status smp_sketch_accumulate(smp_ctx* c, const void* A, int64_t lda, const v
     smp_status s = check_block(c, A, lda, B, ldb, nrows);
     if (s != SMP_OK || nrows == 0) return s;
     if (row0 < 0) return fail(c, SMP_EINVAL, "row0 < 0");
+    if (c->p.engine == SMP_ENGINE_TC_FP8) {
+        if (!fp8_block_ok(c, A, lda, B, ldb))
+            return fail(c, SMP_EUNSUPPORTED, "the FP8 sketch needs k <= 1024, 16-byte aligned blocks, lda, ldb % 8 == 0");
+        return check_cuda(c, launch_sketch_fp8(c, A, lda, B, ldb, row0, nrows, nullptr, 0), "smp_sketch_accumulate");
+    }
     const bool bf16 = c->p.dtype == SMP_BF16;
     const bool tc_ok = bf16 ? bf16_block_ok(c, A, lda, B, ldb) : tc_block_ok(c, A, lda, B, ldb);
     if (c->p.engine == SMP_ENGINE_TC && !tc_ok)
@@ -175,6 +182,12 @@ smp_status smp_sketch_accumulate_pi(smp_ctx* c, const void* Pi, int64_t ldp, con
     smp_status s = check_block(c, A, lda, B, ldb, nrows);
     if (s != SMP_OK || nrows == 0) return s;
     if (!Pi || ldp < nrows) return fail(c, SMP_EINVAL, "Pi_blk is null or ldp < nrows");
+    if (c->p.engine == SMP_ENGINE_TC_FP8) {
+        if (!fp8_block_ok(c, A, lda, B, ldb))
+            return fail(c, SMP_EUNSUPPORTED, "the FP8 sketch needs k <= 1024, 16-byte aligned blocks, lda, ldb % 8 == 0");
+        return check_cuda(c, launch_sketch_fp8(c, A, lda, B, ldb, row0, nrows, (const float*)Pi, ldp),
+                          "smp_sketch_accumulate_pi");
+    }
     const bool bf16 = c->p.dtype == SMP_BF16;
     const bool tc_ok = bf16 ? bf16_block_ok(c, A, lda, B, ldb)
                             : tc_block_ok(c, A, lda, B, ldb) && ((uintptr_t)Pi % 16 == 0) && (ldp % 4 == 0);

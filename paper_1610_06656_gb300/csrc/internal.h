@@ -52,6 +52,7 @@ struct smp_ctx {
     cudaStream_t gen_stream = nullptr;
     cudaEvent_t pi_ready[2] = {nullptr, nullptr};   // recorded on gen_stream after a buffer's generation
     cudaEvent_t pi_free[2] = {nullptr, nullptr};    // recorded on stream after the sketch that read a buffer
+    void* fp8_ws = nullptr;          // FP8 engine: block maxima, scales, completion counter
     int pi_last = -1;                // buffer the last tensor-core sketch read
     int64_t pi_last_rows = 0;        // largest row block sketched so far
     std::string err;
@@ -85,7 +86,7 @@ bool tc_supported(const smp_ctx* c);
 void release_tc(smp_ctx* c);   // waits for the side stream, frees the Pi buffers, stream and events
 cudaError_t tc_speculate_first_block(smp_ctx* c);   // after a reset: Pi of rows [0, last block size) ahead of time
 // Generated Pi of the tensor-core engines: kpad rows (a multiple of 256, zero beyond k) x ld columns (row stride),
-// esize bytes per element (4: TF32 in binary32 containers, 2: BF16).
+// esize bytes per element (4: TF32 in binary32 containers, 2: BF16, 1: E4M3).
 struct PiGeom {
     int kpad;
     int64_t ld;
@@ -101,6 +102,11 @@ cudaError_t pi_release(smp_ctx* c, int b, int64_t row0, int64_t nrows);
 // A caller's Pi (k x nrows binary32, row stride ldp) rounded into a Pi buffer (BF16 contexts); the buffer is then
 // released with pi_release like a generated one.
 cudaError_t pi_import(smp_ctx* c, const float* Pi, int64_t ldp, int64_t nrows, int* buf);
+
+// sketch_fp8.cu
+bool fp8_block_ok(const smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb);
+cudaError_t launch_sketch_fp8(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t row0,
+                              int64_t nrows, const float* Pi, int64_t ldp);
 
 // sketch_bf16.cu
 bool bf16_tc_supported(const smp_ctx* c);

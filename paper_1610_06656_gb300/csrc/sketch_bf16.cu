@@ -38,11 +38,18 @@ constexpr int KGROUP_BYTES = (TILE_M / BOX_COLS) * BOX_BYTES;  // one 8-row grou
 constexpr int DATA_STAGE_BYTES = (KS / 8) * KGROUP_BYTES;    // 128 columns x 32 rows, [8-row group][box]
 constexpr int PI_BOX_BYTES = MMA_N * KS * 2;                 // 256 sketch rows x 32 bf16 (64-byte rows)
 constexpr int PI_STAGE_BYTES = (KC_CTA / MMA_N) * PI_BOX_BYTES;
-constexpr int DSTAGES = 8;
-constexpr int PSTAGES = 4;
+#ifndef SMP_BF16_DSTAGES
+#define SMP_BF16_DSTAGES 8
+#endif
+#ifndef SMP_BF16_PSTAGES
+#define SMP_BF16_PSTAGES 4
+#endif
+constexpr int DSTAGES = SMP_BF16_DSTAGES;   // data tiles (the MMA's A operand)
+constexpr int PSTAGES = SMP_BF16_PSTAGES;   // Pi tiles
 constexpr int DRING_BYTES = DSTAGES * DATA_STAGE_BYTES;
 constexpr int PRING_BYTES = PSTAGES * PI_STAGE_BYTES;
-constexpr int SMEM_BYTES = DRING_BYTES + PRING_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+constexpr int BAR_BYTES = 8 * (2 * (DSTAGES + PSTAGES) + 1) + 8;   // mbarriers, TMEM address, abort flag
+constexpr int SMEM_BYTES = DRING_BYTES + PRING_BYTES + 1024 /* alignment */ + BAR_BYTES;
 static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 constexpr int THREADS = 256;         // 8 warps: data producer 0, MMA 1, Pi producer 2, norm warps 3, 4, 6, 7
 constexpr int NNORM = 4;

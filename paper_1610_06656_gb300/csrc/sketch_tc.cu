@@ -18,6 +18,7 @@
 //     with tcgen05.ld and add the tile into the split's partial sketch. Every wait is bounded (%globaltimer); a
 //     timeout sets the device error word and the CTA unwinds.
 #include <cuda.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -61,10 +62,11 @@ constexpr int PI_STAGE_BYTES = (MAX_KC / PI_BOX_ROWS) * PI_BOX_BYTES;
 constexpr int DRING_BYTES = DSTAGES * DATA_STAGE_BYTES;
 constexpr int ARING_BYTES = ASTAGES * A_STAGE_BYTES;
 constexpr int PRING_BYTES = PSTAGES * PI_STAGE_BYTES;
-constexpr int SMEM_BYTES = DRING_BYTES + ARING_BYTES + PRING_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+constexpr int BAR_BYTES = 8 * (2 * (DSTAGES + ASTAGES + PSTAGES) + 1) + 8;   // mbarriers, TMEM address, abort flag
+constexpr int SMEM_BYTES = DRING_BYTES + ARING_BYTES + PRING_BYTES + 1024 /* alignment */ + BAR_BYTES;
 static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 constexpr int PI_GEN_SMEM = 8192;  // see generate_pi
-constexpr int PI_ROW_PAD = 32;     // Pi buffers: rows padded to a multiple of 32 (both engines' stage heights)
+constexpr int PI_ROW_PAD = 64;     // Pi buffers: rows padded to a multiple of 64 (every engine's stage height)
 constexpr int THREADS = 512;       // 16 warps: producers 0 and 2, MMA 1, copy warps on schedulers 0, 2, 3
 constexpr int NCOPY = 8;           // copy warps: (32-column box, 8-row group) pairs
 // copy warp c (0..7) is warp COPY_WARP[c]: warp ids 4, 6, 7, 8, 10, 11, 12, 14 live on schedulers 0, 2, 3 (id % 4),
@@ -91,6 +93,7 @@ __device__ __forceinline__ float to_tf32(float x) {
 
 __device__ __forceinline__ void store_pi(float* p, float z) { *p = to_tf32(z); }
 __device__ __forceinline__ void store_pi(__nv_bfloat16* p, float z) { *p = __float2bfloat16_rn(z); }
+__device__ __forceinline__ void store_pi(__nv_fp8_e4m3* p, float z) { *p = __nv_fp8_e4m3(z); }
 
 // pi[a][t] (ld = ldp) = Pi(a, row0 + t) rounded to the operand type (TF32 in a binary32 container, or BF16) for
 // a < k, t < nrows; 0 for k <= a < kpad or nrows <= t < tpad. One thread per (t, group of four sketch rows): one
@@ -442,7 +445,10 @@ cudaError_t generate_pi(smp_ctx* c, int b, int64_t row0, int64_t nrows) {
     const dim3 g((unsigned)((tpad + 255) / 256), (unsigned)(gm.kpad / 4));
     const uint32_t k0 = (uint32_t)c->p.seed, k1 = (uint32_t)(c->p.seed >> 32);
     const float scale = (float)(1.0 / std::sqrt((double)k));
-    if (gm.esize == 2)
+    if (gm.esize == 1)   // E4M3 of the N(0, 1) normals; the sketch kernel applies 1 / sqrt(k)
+        pi_gen_kernel<__nv_fp8_e4m3><<<smp::counted(g), 256, PI_GEN_SMEM, c->gen_stream>>>(
+            (__nv_fp8_e4m3*)c->pi_buf[b], gm.ld, k, gm.kpad, row0, nrows, tpad, k0, k1, 1.f);
+    else if (gm.esize == 2)
         pi_gen_kernel<__nv_bfloat16><<<smp::counted(g), 256, PI_GEN_SMEM, c->gen_stream>>>(
             (__nv_bfloat16*)c->pi_buf[b], gm.ld, k, gm.kpad, row0, nrows, tpad, k0, k1, scale);
     else
@@ -462,7 +468,7 @@ PiGeom pi_geom(const smp_ctx* c) {
     PiGeom g;
     g.kpad = (int)round_up(round_up(c->p.k, 16), 256);
     g.ld = round_up(c->max_rows, PI_ROW_PAD);
-    g.esize = c->p.dtype == SMP_BF16 ? 2 : 4;
+    g.esize = c->p.engine == SMP_ENGINE_TC_FP8 ? 1 : (c->p.dtype == SMP_BF16 ? 2 : 4);
     return g;
 }
 
@@ -495,14 +501,16 @@ cudaError_t pi_release(smp_ctx* c, int b, int64_t row0, int64_t nrows) {
 }
 
 namespace {
-// dst[a][t] (ld) = src[a][t] (ldp) rounded to BF16 for a < k, t < nrows; zeros elsewhere up to kpad x tpad.
-__global__ void pi_import_bf16_kernel(const float* __restrict__ src, int64_t ldp, int k, int64_t nrows,
-                                      __nv_bfloat16* dst, int64_t ld, int kpad, int64_t tpad) {
+// dst[a][t] (ld) = src[a][t] (ldp) rounded to the operand type (BF16 or E4M3) for a < k, t < nrows; zeros
+// elsewhere up to kpad x tpad.
+template <typename TP>
+__global__ void pi_import_kernel(const float* __restrict__ src, int64_t ldp, int k, int64_t nrows, TP* dst,
+                                 int64_t ld, int kpad, int64_t tpad) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int a = blockIdx.y;
     if (t >= tpad || a >= kpad) return;
     const float v = (a < k && t < nrows) ? src[(int64_t)a * ldp + t] : 0.f;
-    dst[(int64_t)a * ld + t] = __float2bfloat16_rn(v);
+    store_pi(dst + (int64_t)a * ld + t, v);
 }
 }  // namespace
 
@@ -518,9 +526,15 @@ cudaError_t pi_import(smp_ctx* c, const float* Pi, int64_t ldp, int64_t nrows, i
     c->pi_row0[b] = -1;
     c->pi_nrows[b] = 0;
     const int64_t tpad = round_up(nrows, PI_ROW_PAD);
-    if (gm.esize != 2) return cudaErrorInvalidValue;
-    pi_import_bf16_kernel<<<smp::counted(dim3((unsigned)((tpad + 255) / 256), (unsigned)gm.kpad)), 256, 0,
-                            c->stream>>>(Pi, ldp, c->p.k, nrows, (__nv_bfloat16*)c->pi_buf[b], gm.ld, gm.kpad, tpad);
+    const dim3 grid((unsigned)((tpad + 255) / 256), (unsigned)gm.kpad);
+    if (gm.esize == 2)
+        pi_import_kernel<__nv_bfloat16><<<smp::counted(grid), 256, 0, c->stream>>>(
+            Pi, ldp, c->p.k, nrows, (__nv_bfloat16*)c->pi_buf[b], gm.ld, gm.kpad, tpad);
+    else if (gm.esize == 1)
+        pi_import_kernel<__nv_fp8_e4m3><<<smp::counted(grid), 256, 0, c->stream>>>(
+            Pi, ldp, c->p.k, nrows, (__nv_fp8_e4m3*)c->pi_buf[b], gm.ld, gm.kpad, tpad);
+    else
+        return cudaErrorInvalidValue;
     *buf = b;
     return cudaGetLastError();
 }
@@ -534,6 +548,8 @@ cudaError_t tc_speculate_first_block(smp_ctx* c) {
 
 void release_tc(smp_ctx* c) {
     if (c->gen_stream) cudaStreamSynchronize(c->gen_stream);
+    if (c->fp8_ws) cudaFree(c->fp8_ws);
+    c->fp8_ws = nullptr;
     for (int b = 0; b < 2; ++b) {
         if (c->pi_buf[b]) cudaFree(c->pi_buf[b]);
         if (c->pi_ready[b]) cudaEventDestroy(c->pi_ready[b]);

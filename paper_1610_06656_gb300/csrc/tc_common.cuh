@@ -40,14 +40,25 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 
 // One bounded try_wait: the thread may sleep in the hardware until the phase completes or SUSPEND_NS pass (a
 // polling loop without the hint spends issue slots and shared-memory cycles the copy warps and the MMA need).
-constexpr uint32_t SUSPEND_NS = 20000;
+#ifndef SMP_TC_SUSPEND_NS
+#define SMP_TC_SUSPEND_NS 20000
+#endif
+constexpr uint32_t SUSPEND_NS = SMP_TC_SUSPEND_NS;   // 0: try_wait with the hardware's own time limit
 __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
     uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity), "r"(SUSPEND_NS)
-        : "memory");
+    if (SUSPEND_NS == 0)
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, "
+            "p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity), "r"(SUSPEND_NS)
+            : "memory");
     return ok != 0;
 }
 
@@ -138,6 +149,20 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// Instruction descriptor, kind::f8f6f4 with E4M3 operands (type code 0 in bits 7-9, 10-12), D = F32, A MN-major
+// when a_mn, B K-major.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N, bool a_mn) {
+    return (1u << 4) | ((a_mn ? 1u : 0u) << 15) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
