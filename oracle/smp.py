@@ -259,22 +259,37 @@ def waltmin(n1, n2, rows, cols, vals, qhat, r, T, sA, split=SPLIT_NONE, split_se
     return U, V
 
 
-def canonical(U, V):
-    """Canonical form of U V^T: QR(U) = Qu Ru, QR(V) = Qv Rv, SVD(Ru Rv^T) = W S Z^T -> (Qu W, S, Qv Z).
+def sign_rule(U, V):
+    """Sign reading of the canonical form: the largest-magnitude entry of each column of U is positive (ties: the
+    lowest row index); the matching column of V flips with it. In place; returns (U, V)."""
+    for c in range(U.shape[1]):
+        i = int(np.argmax(np.abs(U[:, c])))
+        if U[i, c] < 0:
+            U[:, c] = -U[:, c]
+            V[:, c] = -V[:, c]
+    return U, V
 
-    Sign reading: the largest-magnitude entry of each column of U is positive (ties: lowest row index).
-    """
+
+def canonical(U, V):
+    """Canonical form of U V^T: QR(U) = Qu Ru, QR(V) = Qv Rv, SVD(Ru Rv^T) = W S Z^T -> (Qu W, S, Qv Z), with the
+    sign reading of sign_rule."""
     Qu, Ru = np.linalg.qr(U)
     Qv, Rv = np.linalg.qr(V)
     W, S, Zt = np.linalg.svd(Ru @ Rv.T)
-    Uc = Qu @ W
-    Vc = Qv @ Zt.T
-    for c in range(Uc.shape[1]):
-        i = int(np.argmax(np.abs(Uc[:, c])))
-        if Uc[i, c] < 0:
-            Uc[:, c] = -Uc[:, c]
-            Vc[:, c] = -Vc[:, c]
+    Uc, Vc = sign_rule(Qu @ W, Qv @ Zt.T)
     return Uc, S, Vc
+
+
+def sketch_svd(At, Bt, r):
+    """Baseline SVD(A~^T B~) (Section 4, the comparison of SMP-PCA with the SVD of the sketched product): the top-r
+    singular triplets of A~^T B~ (A~ = At: k x n1, B~ = Bt: k x n2). The paper computes them by power iteration
+    without forming the n1 x n2 product (footnote there); power iteration converges to this plain definition, which
+    is written out here: the dense product in binary64, its LAPACK SVD truncated to r, the sign reading of
+    sign_rule."""
+    M = np.asarray(At, dtype=np.float64).T @ np.asarray(Bt, dtype=np.float64)
+    W, S, Zt = np.linalg.svd(M, full_matrices=False)
+    U, V = sign_rule(W[:, :r].copy(), Zt[:r].T.copy())
+    return U, S[:r].copy(), V
 
 
 def spectral_error(M, U, S, V):

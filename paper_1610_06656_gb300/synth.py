@@ -8,6 +8,10 @@ Generators:
     X (n1 x L), Y (n2 x L), N1, N2 i.i.d. N(0, 1); column j (0-based) of each matrix is multiplied by
     (j + 1)^-alpha. With same_ab the call returns A only (the PCA case A = B, Section 3, Remark 3).
   * the paper's synthetic matrix G D, G i.i.d. N(0, 1), D_ii = 1/i (Section 4, "Description of datasets").
+  * unit columns drawn from a cone of half-angle theta around one direction (Section 4, the comparison with
+    SVD(A~^T B~) and the estimator figure): each column is cos(phi) e + sin(phi) w with e a fixed random unit
+    vector, w a random unit vector orthogonal to e, and phi uniform in [0, theta] (reading: the paper names the
+    cone angle only).
 """
 import numpy as np
 
@@ -66,3 +70,19 @@ def lowrank_plus_noise_torch(d, n1, n2, L, sigma, alpha, seed, device, dtype=Non
             b = (z @ Y.T + sigma * torch.randn(r1 - r0, n2, generator=g, device=device)) * sb
             B[r0:r1] = b.to(dtype)
     return A, B, Z, X, Y
+
+
+def cone(d, n1, n2, theta, seed, dtype=np.float64):
+    """A (d x n1) and B (d x n2) with unit columns at angle phi ~ U[0, theta] from one shared random direction."""
+    rng = np.random.default_rng(seed)
+    e = rng.standard_normal(d)
+    e /= np.linalg.norm(e)
+
+    def draw(n):
+        W = rng.standard_normal((d, n))
+        W -= np.outer(e, e @ W)
+        W /= np.linalg.norm(W, axis=0)
+        phi = rng.uniform(0.0, theta, size=n)
+        return (np.outer(e, np.cos(phi)) + W * np.sin(phi)).astype(dtype)
+
+    return draw(n1), draw(n2)
