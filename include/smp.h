@@ -7,6 +7,7 @@
  *   smp_sample                                                       step 3: Omega by Eq. (1)
  *   smp_estimate                                                     step 4: M~ over Omega by Eq. (2)
  *   smp_waltmin                                                      step 5: Algorithm 2 (Appendix A)
+ *   smp_sketch_svd                     the baseline SVD(At^T Bt) of Section 4, from the same finalized sketches
  *
  * Conventions shared by every call:
  *   - Pointers named *_dev are CUDA device pointers owned by the caller unless stated otherwise. Pointers
@@ -169,6 +170,20 @@ smp_status smp_estimate(smp_ctx* ctx, void* vals_dev);
  * Synchronises. Errors: SMP_ESTATE, SMP_EINVAL, SMP_ENUMERIC, SMP_ENOMEM. */
 smp_status smp_waltmin(smp_ctx* ctx, const void* vals_dev, int32_t r, int32_t T, uint32_t flags, uint64_t seed,
                        const double* U_init_dev, double* U_dev, double* S_dev, double* V_dev);
+
+/* Baseline SVD(At^T Bt) (Section 4, the comparison of SMP-PCA with the SVD of the sketched product): the top-r
+ * singular triplets of M = At^T Bt (At = Pi A: k x n1, Bt = Pi B: k x n2, the finalized sketches), by block power
+ * iteration through the factors without forming the n1 x n2 product (the footnote there). Block of b =
+ * min(2r + 8, 64, n1, n2, k) columns, Philox start block on the right (counter (j, 0, c/4, 4) under key seed),
+ * orthonormalised by Cholesky-QR; each iteration Y = M Z, Y orthonormalised, Z = M^T Y. Every second (binary32
+ * sketches) or fourth (binary64) iteration the top-r Ritz vectors U = Y E_r (E: eigenvectors of Z^T Z, binary64
+ * Jacobi) are compared with the previous check's; the iteration stops when they move by less than 2e-5 (1e-11)
+ * in sqrt(r - ||U^T U_prev||_F^2), or after 200 (400) iterations. Output: U = Y E_r, S = sqrt(eigenvalues),
+ * V = Z E_r / S, the largest-magnitude entry of each U column made positive. Products in the sketch precision
+ * (binary32 or binary64), reductions over the long dimension finished in binary64.
+ * 1 <= r <= 32, r <= min(n1, n2, k). Outputs (device, double, row-major): U_dev n1 x r, S_dev r, V_dev n2 x r.
+ * Synchronises. Errors: SMP_ESTATE (sketch not finalized), SMP_EINVAL, SMP_ENOMEM. */
+smp_status smp_sketch_svd(smp_ctx* ctx, int32_t r, uint64_t seed, double* U_dev, double* S_dev, double* V_dev);
 
 /* Block until the context's stream is idle and report any device-side error word. */
 smp_status smp_sync(smp_ctx* ctx);

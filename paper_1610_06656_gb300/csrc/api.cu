@@ -311,6 +311,15 @@ smp_status smp_waltmin(smp_ctx* c, const void* vals, int32_t r, int32_t T, uint3
     return run_waltmin(c, vals, r, T, flags, seed, U_init, U, S, V);
 }
 
+smp_status smp_sketch_svd(smp_ctx* c, int32_t r, uint64_t seed, double* U, double* S, double* V) {
+    if (!c) return fail(nullptr, SMP_EINVAL, "null context");
+    if (!c->finalized) return fail(c, SMP_ESTATE, "smp_sketch_svd before finalize");
+    if (r < 1 || r > 32 || r > c->p.n1 || r > c->p.n2 || r > c->p.k)
+        return fail(c, SMP_EINVAL, "r out of [1, min(32, n1, n2, k)]");
+    if (!U || !S || !V) return fail(c, SMP_EINVAL, "null output");
+    return run_sketch_svd(c, r, seed, U, S, V);
+}
+
 smp_status smp_sync(smp_ctx* c) {
     if (!c) return fail(nullptr, SMP_EINVAL, "null context");
     smp_status s = check_cuda(c, cudaStreamSynchronize(c->stream), "smp_sync");

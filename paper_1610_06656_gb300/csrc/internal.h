@@ -126,6 +126,7 @@ smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out);
 cudaError_t launch_estimate(smp_ctx* c, void* vals);
 
 // waltmin.cu
+smp_status run_sketch_svd(smp_ctx* c, int r, uint64_t seed, double* U, double* S, double* V);
 smp_status run_waltmin(smp_ctx* c, const void* vals, int r, int T, uint32_t flags, uint64_t seed,
                        const double* U_init, double* U, double* S, double* V);
 

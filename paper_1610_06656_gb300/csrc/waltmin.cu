@@ -638,6 +638,17 @@ void cholqr2(const TX* X, int64_t n, int b, TQ* Q, double* part, double* G, doub
     if (Rout) upper_mul_kernel<<<smp::counted(nblocks(b * b, 256)), 256, 0, st>>>(R2, R1, b, Rout);
 }
 
+// The Jacobi eigen kernel takes up to 2 MAX_SMALL (MAX_SMALL + 1) elements of dynamic shared memory.
+void jacobi_smem_attr() {
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(jacobi_eig_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         2 * MAX_SMALL * (MAX_SMALL + 1) * 8);
+    cudaFuncSetAttribute(jacobi_eig_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         2 * MAX_SMALL * (MAX_SMALL + 1) * 4);
+    done = true;
+}
+
 struct Segments {
     int64_t* start = nullptr;   // [n_out + 1]
     int64_t* b = nullptr;       // [nseg]
@@ -849,14 +860,7 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
     TY* Yp = ar.take<TY>(nseg_max * (int64_t)b);
     double* Gc = ar.take<double>(nmax * (int64_t)(r * (r + 1) / 2 + r));
 
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(jacobi_eig_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             2 * MAX_SMALL * (MAX_SMALL + 1) * 8);
-        cudaFuncSetAttribute(jacobi_eig_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             2 * MAX_SMALL * (MAX_SMALL + 1) * 4);
-        attr_done = true;
-    }
+    jacobi_smem_attr();
 
     // segments (Omega is fixed for the whole call); the count copy is the call's only early host sync
     seg_count_kernel<<<smp::counted(nblocks(n1, 256)), 256, 0, st>>>(c->row_ptr, n1, seg_cnt);
@@ -996,7 +1000,254 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
     return status;
 }
 
+// ---------------------------------------------------------------------------------------------------------------
+// Baseline SVD(A~^T B~) (Section 4, the comparison with the SVD of the sketched product): block power iteration on
+// M = A~^T B~ through its factors, the n1 x n2 product never formed (the footnote there)
+// ---------------------------------------------------------------------------------------------------------------
+constexpr int SK_ROWS = 256;   // rows of X per CTA of the reduction X^T Y
+constexpr int SK_BMAX = 64;    // block columns
+
+// part[blk][a][c] = sum over the rows i of CTA row block blk of X[i][a] Y[i][c] (a < k, c < b <= 64). CTA (32
+// sketch rows a, one row block); thread (a = tid % 32, group of 8 columns c = tid / 32); X and Y staged 32 rows at
+// a time.
+template <typename TS, typename TY>
+__global__ void __launch_bounds__(256) xty_partial_kernel(const TS* __restrict__ X, int64_t ldx, int k,
+                                                          const TY* __restrict__ Y, int64_t n, int b, TY* part) {
+    __shared__ TY xs[32][33];
+    __shared__ TY ys[32][SK_BMAX + 1];
+    const int tid = threadIdx.x, al = tid & 31, cg = tid >> 5;
+    const int a0 = blockIdx.x * 32;
+    const int64_t i0 = (int64_t)blockIdx.y * SK_ROWS, i1 = min(n, i0 + SK_ROWS);
+    TY acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = TY(0);
+    for (int64_t ib = i0; ib < i1; ib += 32) {
+        __syncthreads();
+        for (int e = tid; e < 32 * 32; e += 256) {
+            const int rr = e >> 5, aa = e & 31;
+            const int64_t i = ib + rr;
+            xs[rr][aa] = (i < i1 && a0 + aa < k) ? (TY)X[i * ldx + a0 + aa] : TY(0);
+        }
+        for (int e = tid; e < 32 * SK_BMAX; e += 256) {
+            const int rr = e / SK_BMAX, cc = e % SK_BMAX;
+            const int64_t i = ib + rr;
+            ys[rr][cc] = (i < i1 && cc < b) ? Y[i * b + cc] : TY(0);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int rr = 0; rr < 32; ++rr) {
+            const TY x = xs[rr][al];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] = fma(x, ys[rr][cg * 8 + q], acc[q]);
+        }
+    }
+    const int a = a0 + al;
+    if (a >= k) return;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        if (cg * 8 + q < b) part[((int64_t)blockIdx.y * k + a) * b + cg * 8 + q] = acc[q];
+}
+
+// W[e] = sum over blk of part[blk][e] (fixed order, binary64), e < len.
+template <typename TY>
+__global__ void part_sum_kernel(const TY* __restrict__ part, int nblk, int64_t len, TY* W) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= len) return;
+    double s = 0.0;
+    for (int q = 0; q < nblk; ++q) s += (double)part[q * len + e];
+    W[e] = (TY)s;
+}
+
+// Out[j][c] = sum over a < k of X[j][a] W[a][c] (j < n, c < b <= 64). CTA of 32 rows j; thread (j = tid % 32,
+// group of 8 columns); X and W staged 32 sketch rows at a time.
+template <typename TS, typename TY>
+__global__ void __launch_bounds__(256) xw_kernel(const TS* __restrict__ X, int64_t ldx, int k,
+                                                 const TY* __restrict__ W, int64_t n, int b, TY* Out) {
+    __shared__ TY xs[32][33];
+    __shared__ TY ws[32][SK_BMAX + 1];
+    const int tid = threadIdx.x, jl = tid & 31, cg = tid >> 5;
+    const int64_t j0 = (int64_t)blockIdx.x * 32;
+    TY acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = TY(0);
+    for (int ab = 0; ab < k; ab += 32) {
+        __syncthreads();
+        for (int e = tid; e < 32 * 32; e += 256) {
+            const int rr = e >> 5, aa = e & 31;
+            const int64_t j = j0 + rr;
+            xs[rr][aa] = (j < n && ab + aa < k) ? (TY)X[j * ldx + ab + aa] : TY(0);
+        }
+        for (int e = tid; e < 32 * SK_BMAX; e += 256) {
+            const int aa = e / SK_BMAX, cc = e % SK_BMAX;
+            ws[aa][cc] = (ab + aa < k && cc < b) ? W[(int64_t)(ab + aa) * b + cc] : TY(0);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int aa = 0; aa < 32; ++aa) {
+            const TY x = xs[jl][aa];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] = fma(x, ws[aa][cg * 8 + q], acc[q]);
+        }
+    }
+    const int64_t j = j0 + jl;
+    if (j >= n) return;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        if (cg * 8 + q < b) Out[j * b + cg * 8 + q] = acc[q];
+}
+
+// V[i][c] /= sigma_c with sigma_c = sqrt(lambda_c) (a zero or negative lambda leaves a zero column); S = sigma.
+__global__ void ritz_scale_kernel(double* V, int64_t n2, int r, const double* __restrict__ ev, double* S) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < r) S[e] = sqrt(fmax(ev[e], 0.0));
+    if (e >= n2 * r) return;
+    const int c = (int)(e % r);
+    const double sg = sqrt(fmax(ev[c], 0.0));
+    V[e] = sg > 0.0 ? V[e] / sg : 0.0;
+}
+
+template <typename TS, typename TY>
+struct SketchOp {
+    const TS* At;   // n1 x ldk: row i = A~ column i
+    const TS* Bt;   // n2 x ldk
+    int64_t n1, n2, ldk;
+    int k, b;
+    TY* W;          // k x b
+    TY* part;       // row blocks x k x b
+    cudaStream_t st;
+
+    void xty(const TS* X, const TY* Y, int64_t n) const {
+        const int nblk = (int)std::max<int64_t>(1, (n + SK_ROWS - 1) / SK_ROWS);
+        xty_partial_kernel<TS, TY><<<smp::counted(dim3((unsigned)((k + 31) / 32), (unsigned)nblk)), 256, 0, st>>>(
+            X, ldk, k, Y, n, b, part);
+        part_sum_kernel<TY><<<smp::counted(nblocks((int64_t)k * b, 256)), 256, 0, st>>>(part, nblk, (int64_t)k * b,
+                                                                                      W);
+    }
+    void xw(const TS* X, int64_t n, TY* Out) const {
+        xw_kernel<TS, TY><<<smp::counted(nblocks(n, 32)), 256, 0, st>>>(X, ldk, k, W, n, b, Out);
+    }
+    void apply(const TY* Z, TY* Y) const {   // Y (n1 x b) = A~^T (B~ Z)
+        xty(Bt, Z, n2);
+        xw(At, n1, Y);
+    }
+    void apply_t(const TY* Y, TY* Z) const {   // Z (n2 x b) = B~^T (A~ Y)
+        xty(At, Y, n1);
+        xw(Bt, n2, Z);
+    }
+};
+
+template <typename TS, typename TY>
+smp_status sketch_svd_typed(smp_ctx* c, int r, uint64_t seed, double* U, double* S, double* V) {
+    const int64_t n1 = c->p.n1, n2 = c->p.n2, nmax = std::max(n1, n2);
+    const int k = c->p.k;
+    cudaStream_t st = c->stream;
+    const int b = (int)std::min<int64_t>(std::min<int64_t>(2 * r + 8, SK_BMAX), std::min<int64_t>(std::min(n1, n2), k));
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const int64_t skblk = std::max<int64_t>(1, (nmax + SK_ROWS - 1) / SK_ROWS);
+    const int64_t gblk = std::max<int64_t>(1, (nmax + GRAM_ROWS_PER_BLOCK - 1) / GRAM_ROWS_PER_BLOCK);
+    size_t need = 0;
+    auto add = [&](int64_t n, size_t sz) { need += ((size_t)std::max<int64_t>(n, 1) * sz + 511) & ~size_t(255); };
+    add(n1 * b, sizeof(TY));                          // Y
+    add(n2 * b, sizeof(TY));                          // Z
+    add((int64_t)k * b, sizeof(TY));                  // W
+    add(skblk * k * b, sizeof(TY));                   // reduction partials
+    add(gblk * MAX_SMALL * MAX_SMALL, 8);             // Gram partials
+    add(4 * b * b + 4 * b, 8);                        // G, R1, R2, E, eigenvalues
+    add(2 * n1 * r + r * r, 8);                       // Ritz vectors now and at the previous check, their Gram
+    void* ws = nullptr;
+    if (cudaMallocAsync(&ws, need, st) != cudaSuccess) return fail(c, SMP_ENOMEM, "smp_sketch_svd: scratch");
+    Arena ar{(char*)ws, 0, need};
+    TY* Y = ar.take<TY>(n1 * b);
+    TY* Z = ar.take<TY>(n2 * b);
+    SketchOp<TS, TY> op;
+    op.At = (const TS*)c->sk;
+    op.Bt = c->p.same_ab ? op.At : op.At + n1 * c->ldk;
+    op.n1 = n1;
+    op.n2 = n2;
+    op.ldk = c->ldk;
+    op.k = k;
+    op.b = b;
+    op.st = st;
+    op.W = ar.take<TY>((int64_t)k * b);
+    op.part = ar.take<TY>(skblk * k * b);
+    double* gpart = ar.take<double>(gblk * MAX_SMALL * MAX_SMALL);
+    double* G = ar.take<double>(b * b);
+    double* R1 = ar.take<double>(b * b);
+    double* R2 = ar.take<double>(b * b);
+    double* E = ar.take<double>(b * b);
+    double* ev = ar.take<double>(4 * b);
+    double* U0p = ar.take<double>(n1 * r);
+    double* Gx = ar.take<double>(r * r);
+    jacobi_smem_attr();
+
+    // Philox start block on the right (TAG_INIT), orthonormalised
+    start_block_kernel<TY><<<smp::counted(nblocks(n2 * ((b + 3) / 4), 256)), 256, 0, st>>>(n2, b, k0, k1, Z);
+    cholqr2<TY, TY, TY>(Z, n2, b, Z, gpart, G, R1, R2, nullptr, st);
+    // Each iteration: Y = M Z, orthonormalise Y, Z = M^T Y. Every `every` iterations the top-r Ritz vectors
+    // Y E_r (E: eigenvectors of Z^T Z, binary64 Jacobi) are compared with those of the previous check; the
+    // iteration stops once they move by less than tol (sqrt(r - ||U0^T U0prev||_F^2)).
+    const bool dbl = sizeof(TY) == 8;
+    const int max_iter = dbl ? 400 : 200, every = dbl ? 4 : 2;
+    const double tol = dbl ? 1e-11 : 2e-5;
+    smp_status status = SMP_OK;
+    bool have_prev = false;
+    for (int it = 1; it <= max_iter; ++it) {
+        const bool check = it % every == 0 || it == max_iter;
+        op.apply(Z, Y);
+        if (check) {
+            cholqr2<TY, TY, TY>(Y, n1, b, Y, gpart, G, R1, R2, nullptr, st);
+        } else {
+            gram_chol<TY>(Y, n1, b, gpart, G, R1, st);
+            apply_rinv<TY, TY, TY>(Y, n1, b, R1, Y, st);
+        }
+        op.apply_t(Y, Z);
+        if (check) {
+            gram<TY, TY>(Z, Z, n2, b, b, gpart, G, st);
+            launch_jacobi<double>(G, b, 4e-15, 40, ev, E, st);
+            ritz_kernel<TY><<<smp::counted(nblocks(n1 * r, 256)), 256, 0, st>>>(Y, E, n1, b, r, U);
+            bool done = false;
+            if (have_prev) {
+                gram<double, double>(U, U0p, n1, r, r, gpart, Gx, st);
+                std::vector<double> hx(r * r);
+                cudaError_t e1 = cudaMemcpyAsync(hx.data(), Gx, sizeof(double) * r * r, cudaMemcpyDeviceToHost, st);
+                if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(st);
+                if (e1 != cudaSuccess) {
+                    status = check_cuda(c, e1, "smp_sketch_svd check");
+                    break;
+                }
+                double fro = 0.0;
+                for (double v : hx) fro += v * v;
+                done = std::sqrt(std::max(0.0, (double)r - fro)) < tol;
+            }
+            have_prev = true;
+            if (done || it == max_iter) {
+                // M ~ Y Y^T M = Y Z^T = (Y E)(Z E)^T, and Z E has orthogonal columns of norms sqrt(lambda)
+                ritz_kernel<TY><<<smp::counted(nblocks(n2 * r, 256)), 256, 0, st>>>(Z, E, n2, b, r, V);
+                ritz_scale_kernel<<<smp::counted(nblocks(std::max<int64_t>(n2 * r, r), 256)), 256, 0, st>>>(
+                    V, n2, r, ev, S);
+                sign_kernel<<<smp::counted(r), 256, 0, st>>>(U, n1, V, n2, r);
+                break;
+            }
+            cudaMemcpyAsync(U0p, U, sizeof(double) * n1 * r, cudaMemcpyDeviceToDevice, st);
+        }
+        gram_chol<TY>(Z, n2, b, gpart, G, R1, st);
+        apply_rinv<TY, TY, TY>(Z, n2, b, R1, Z, st);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (status == SMP_OK && e != cudaSuccess) status = check_cuda(c, e, "smp_sketch_svd kernels");
+    cudaFreeAsync(ws, st);
+    e = cudaStreamSynchronize(st);
+    if (status == SMP_OK && e != cudaSuccess) status = check_cuda(c, e, "smp_sketch_svd sync");
+    if (status == SMP_OK) status = read_device_error(c);
+    return status;
+}
+
 }  // namespace
+
+smp_status run_sketch_svd(smp_ctx* c, int r, uint64_t seed, double* U, double* S, double* V) {
+    if (c->acc_bytes == 8) return sketch_svd_typed<double, double>(c, r, seed, U, S, V);
+    return sketch_svd_typed<float, float>(c, r, seed, U, S, V);
+}
 
 smp_status run_waltmin(smp_ctx* c, const void* vals, int r, int T, uint32_t flags, uint64_t seed,
                        const double* U_init, double* U, double* S, double* V) {

@@ -65,6 +65,14 @@ class Solver:
         S.smp_waltmin(self.ctx, vals, r, T, flags, seed, U_init, U, Sv, V)
         return U, Sv, V
 
+    def sketch_svd(self, r, seed=4):
+        """Baseline SVD(At^T Bt) of the finalized sketches (smp_sketch_svd): U (n1 x r), S (r), V (n2 x r)."""
+        U = torch.empty(self.n1, r, dtype=torch.float64, device="cuda")
+        Sv = torch.empty(r, dtype=torch.float64, device="cuda")
+        V = torch.empty(self.n2, r, dtype=torch.float64, device="cuda")
+        S.smp_sketch_svd(self.ctx, r, seed, U, Sv, V)
+        return U, Sv, V
+
     def solve(self, A, B, r, T, m=None, sample_seed=2, walt_seed=3, flags=0, block_rows=65536):
         m = default_m(self.n1, self.n2, r) if m is None else m
         self.sketch(A, B, block_rows)

@@ -42,6 +42,7 @@ SIGNATURES = {
                               _c.POINTER(_vp), _c.POINTER(_vp), _c.POINTER(_vp)]),
     "smp_estimate": (_i32, [_vp, _vp]),
     "smp_waltmin": (_i32, [_vp, _vp, _i32, _i32, _u32, _u64, _vp, _vp, _vp, _vp]),
+    "smp_sketch_svd": (_i32, [_vp, _i32, _u64, _vp, _vp, _vp]),
     "smp_sync": (_i32, [_vp]),
     "smp_destroy": (_i32, [_vp]),
     "smp_last_error": (_c.c_char_p, [_vp]),
@@ -173,6 +174,11 @@ def smp_omega_view(ctx):
 
 def smp_estimate(ctx, vals):
     _check(load().smp_estimate(ctx, _ptr(vals)), "smp_estimate", ctx)
+
+
+def smp_sketch_svd(ctx, r, seed, U, S, V):
+    _check(load().smp_sketch_svd(ctx, r, seed & 0xFFFFFFFFFFFFFFFF, _ptr(U), _ptr(S), _ptr(V)), "smp_sketch_svd",
+           ctx)
 
 
 def smp_waltmin(ctx, vals, r, T, flags, seed, U_init, U, S, V):

@@ -137,8 +137,11 @@ def test_sketch_identity_pi_is_exact(env):
     assert nnz == 24 * 30
     vals = s.estimate(nnz).cpu().numpy()
     om = omega_numpy(s)
+    rows, cols = np.repeat(np.arange(24), 30), np.tile(np.arange(30), 24)   # every entry, row-major
+    np.testing.assert_array_equal(csr_rows(om["row_ptr"]), rows)
+    np.testing.assert_array_equal(om["col"], cols)
     M = A.astype(np.float64).T @ B.astype(np.float64)
-    np.testing.assert_allclose(vals, M[csr_rows(om["row_ptr"]), om["col"]], rtol=2e-6, atol=1e-6 * np.abs(M).max())
+    np.testing.assert_allclose(vals, M[rows, cols], rtol=2e-6, atol=1e-6 * np.abs(M).max())
     s.close()
 
 
@@ -243,10 +246,13 @@ def test_estimate_matches_oracle(env, data):
                           torch.from_numpy(ref.sA).cuda(), torch.from_numpy(ref.sB).cuda())
     nnz = s.sample(O.default_m(N1, N2, R), seed=3)
     vals = s.estimate(nnz).cpu().numpy().astype(np.float64)
+    # the oracle's own Omega (the GPU's equals it bit for bit) indexes the oracle's estimate
+    rows, cols, _ = O.sample_omega(ref.sA, ref.sB, O.default_m(N1, N2, R), 3)
     om = omega_numpy(s)
-    rows = csr_rows(om["row_ptr"])
-    want = O.estimate(rows, om["col"], At32.T.astype(np.float64), Bt32.T.astype(np.float64), ref.sA, ref.sB)
-    scale = np.sqrt(ref.sA[rows] * ref.sB[om["col"]])
+    np.testing.assert_array_equal(csr_rows(om["row_ptr"]), rows)
+    np.testing.assert_array_equal(om["col"], cols)
+    want = O.estimate(rows, cols, At32.T.astype(np.float64), Bt32.T.astype(np.float64), ref.sA, ref.sB)
+    scale = np.sqrt(ref.sA[rows] * ref.sB[cols])
     assert np.max(np.abs(vals - want) / scale) < 2e-6
     s.close()
 
@@ -263,9 +269,13 @@ def _waltmin_setup(env, data, seed=31):
                           torch.from_numpy(ref.sA).cuda(), torch.from_numpy(ref.sB).cuda())
     m = O.default_m(N1, N2, R)
     s.sample(m, seed=5)
-    om = omega_numpy(s)
-    rows = csr_rows(om["row_ptr"])
-    vals32 = O.estimate(rows, om["col"], At32.T.astype(np.float64), Bt32.T.astype(np.float64), ref.sA,
+    # the oracle's own Omega (the GPU's equals it bit for bit) feeds the oracle's estimate and WAltMin
+    rows, cols, qh = O.sample_omega(ref.sA, ref.sB, m, 5)
+    og = omega_numpy(s)
+    np.testing.assert_array_equal(csr_rows(og["row_ptr"]), rows)
+    np.testing.assert_array_equal(og["col"], cols)
+    om = dict(col=cols, qhat=qh)
+    vals32 = O.estimate(rows, cols, At32.T.astype(np.float64), Bt32.T.astype(np.float64), ref.sA,
                         ref.sB).astype(np.float32)
     return s, ref, rows, om, vals32
 
