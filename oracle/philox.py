@@ -21,6 +21,7 @@ The paper being implemented only asks for Pi(i, j) ~ N(0, 1/k) i.i.d. (Algorithm
   sample coin    : counter = (i, j, 0, TAG_SAMPLE); u = ((x0 >> 5) * 2^26 + (x1 >> 6)) * 2^-53 in [0, 1)
   split coin     : counter = (i, j, 0, TAG_SPLIT), same 53-bit mapping
   init block     : counter = (i, 0, c // 4, TAG_INIT), same Gaussian mapping as Pi (no 1/sqrt(k))
+  multinomial    : counter = (i, s, 0, TAG_MULTI) for draw s of row i, same 53-bit mapping as the coins
 
 Both uniforms are exact in binary32 and binary64, so the two sides see identical uniforms; they differ only in
 how ln / sqrt / cos / sin are rounded.
@@ -39,6 +40,7 @@ TAG_PI = 1
 TAG_SAMPLE = 2
 TAG_SPLIT = 3
 TAG_INIT = 4
+TAG_MULTI = 5
 
 TWO_M24 = 2.0 ** -24
 TWO_M53 = 2.0 ** -53

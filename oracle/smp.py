@@ -135,6 +135,66 @@ def sample_omega(sA, sB, m, seed):
     return np.concatenate(rows_out), np.concatenate(cols_out), np.concatenate(q_out)
 
 
+PREFIX_BLOCK = 1024
+
+
+def blocked_prefix(x):
+    """Inclusive prefix sums of x in the order both sides of the parity tests follow (a reading: the paper fixes no
+    order): sequential left-to-right sums within blocks of PREFIX_BLOCK elements, each block's sums then offset by the
+    sequential sum of the earlier blocks' totals (one binary64 addition per element; the first block's offset is 0)."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    offset = 0.0
+    for b0 in range(0, x.shape[0], PREFIX_BLOCK):
+        w = np.cumsum(x[b0:b0 + PREFIX_BLOCK])        # np.add.accumulate: strictly left to right
+        out[b0:b0 + PREFIX_BLOCK] = offset + w
+        offset = offset + float(w[-1])
+    return out
+
+
+def sample_omega_multinomial(sA, sB, m, seed):
+    """Row-wise multinomial sampling of Omega (Appendix, "Sampling"), the O(m log n) alternative to the Bernoulli
+    coins. Row i expects m_i = sum_j q_ij draws (q_ij = alpha_i + beta_j of Eq. (1), unclipped) and draws column j
+    with probability q~_ij = q_ij / m_i, located by binary search on the row's CDF, whose entries are a linear
+    shift and scale of one shared prefix sum of beta.
+
+    Readings (binding for both sides):
+      * S_i = n2 alpha_i + Bcum_{n2-1} with Bcum = blocked_prefix(beta); draws per row c_i = floor(S_i + 1/2);
+      * draw s of row i: u = the 53-bit Philox uniform of counter (i, s, 0, TAG_MULTI), t = u S_i, and the column
+        is the smallest j with t < (j + 1) alpha_i + Bcum_j (the last column if none);
+      * Omega is the set of distinct drawn pairs, count_ij the number of draws of (i, j); the effective probability
+        stored with each pair is q^_ij = (c_i ((alpha_i + beta_j) / S_i)) / count_ij, so the WAltMin weight
+        1 / q^_ij = count_ij / (c_i q~_ij) has expectation 1 per entry, as 1 / q^ does for the Bernoulli coins.
+    Every step is one IEEE binary64 operation in the order written. Returns (rows, cols, qhat, counts) in
+    canonical row-major order.
+    """
+    alpha, beta = sampling_terms(sA, sB, m)
+    n1, n2 = alpha.shape[0], beta.shape[0]
+    Bcum = blocked_prefix(beta)
+    jp1 = np.arange(1, n2 + 1, dtype=np.float64)
+    rows_out, cols_out, q_out, c_out = [], [], [], []
+    for i in range(n1):
+        S = float(n2) * alpha[i] + Bcum[-1]
+        c = int(np.floor(S + 0.5))
+        if c == 0:
+            continue
+        u = philox.coin_uniforms(seed, philox.TAG_MULTI, np.uint64(i), np.arange(c, dtype=np.uint64))
+        t = u * S
+        cdf = jp1 * alpha[i] + Bcum                    # non-decreasing: (j + 1) alpha_i + Bcum_j
+        j = np.minimum(np.searchsorted(cdf, t, side="right"), n2 - 1)
+        counts = np.bincount(j, minlength=n2)
+        keep = np.nonzero(counts)[0]
+        cnt = counts[keep]
+        rows_out.append(np.full(keep.shape[0], i, dtype=np.int64))
+        cols_out.append(keep.astype(np.int64))
+        q_out.append((float(c) * ((alpha[i] + beta[keep]) / S)) / cnt.astype(np.float64))
+        c_out.append(cnt.astype(np.int64))
+    if not rows_out:
+        e = np.zeros(0, dtype=np.int64)
+        return e, e, np.zeros(0), e
+    return np.concatenate(rows_out), np.concatenate(cols_out), np.concatenate(q_out), np.concatenate(c_out)
+
+
 # --------------------------------------------------------------------------------------------------------------
 # Step 2b (Algorithm 1, step 4; Eq. (2)): rescaled JL estimate over Omega.
 # --------------------------------------------------------------------------------------------------------------
@@ -310,10 +370,14 @@ def default_m(n1, n2, r):
 
 
 def smp_pca(A, B, r, k, m, T, seed, sample_seed, block_rows=65536, same_ab=False, split=SPLIT_NONE,
-            split_seed=0, pi=None):
-    """Algorithm 1 end to end. Returns a dict with every intermediate and the canonical (U, S, V)."""
+            split_seed=0, pi=None, sampler="bernoulli"):
+    """Algorithm 1 end to end. Returns a dict with every intermediate and the canonical (U, S, V). sampler:
+    "bernoulli" (Eq. (1) coins, step 3) or "multinomial" (the Appendix's row-wise sampling)."""
     st = sketch(A, B, k, seed, block_rows, same_ab, pi)
-    rows, cols, qhat = sample_omega(st.sA, st.sB, m, sample_seed)
+    if sampler == "multinomial":
+        rows, cols, qhat, _ = sample_omega_multinomial(st.sA, st.sB, m, sample_seed)
+    else:
+        rows, cols, qhat = sample_omega(st.sA, st.sB, m, sample_seed)
     vals = estimate(rows, cols, st.At, st.Bt, st.sA, st.sB)
     Uh, Vh = waltmin(st.n1, st.n2, rows, cols, vals, qhat, r, T, st.sA, split, split_seed)
     U, S, V = canonical(Uh, Vh)
