@@ -153,20 +153,21 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
-def spectral_error(torch, A, B, U, S, V, block=65536):
-    """||A^T B - U S V^T||_2 / ||A^T B||_2 with A^T B accumulated blockwise (FP32 products, no TF32, summed in
-    binary64). Evaluation only: torch / cuSOLVER compute the norm, not the path."""
+def spectral_error(torch, A, B, factors, block=65536):
+    """||A^T B - U S V^T||_2 / ||A^T B||_2 for each (U, S, V) in factors, with A^T B accumulated blockwise (FP32
+    products, no TF32, summed in binary64), and the Eckart-Young optimum. Evaluation only: torch / cuSOLVER compute
+    the norms, not the path."""
     prev = torch.backends.cuda.matmul.allow_tf32
     torch.backends.cuda.matmul.allow_tf32 = False
     M = torch.zeros(A.shape[1], B.shape[1], dtype=torch.float64, device=A.device)
     for r0 in range(0, A.shape[0], block):
         M += (A[r0:r0 + block].float().T @ B[r0:r0 + block].float()).double()
     torch.backends.cuda.matmul.allow_tf32 = prev
-    E = M - (U * S) @ V.T
     sv = torch.linalg.svdvals(M)
-    r = U.shape[1]
+    r = factors[0][0].shape[1]
     opt = float(sv[r] / sv[0]) if sv.shape[0] > r else 0.0
-    return float(torch.linalg.matrix_norm(E, ord=2) / sv[0]), opt
+    errs = [float(torch.linalg.matrix_norm(M - (U * S) @ V.T, ord=2) / sv[0]) for U, S, V in factors]
+    return errs, opt
 
 
 def main():
@@ -180,6 +181,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-error", action="store_true")
+    ap.add_argument("--no-baseline", action="store_true",
+                    help="skip the SVD(A~^T B~) and multinomial-sampling comparisons")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -283,9 +286,43 @@ def main():
     roof["launch_ms"] = sk_avg_s * 1e3
     roof["bytes_per_launch"] = sk_bytes
 
+    # the paper's comparison, SVD(A~^T B~) by power iteration on the last step's sketches (outside the timed
+    # region; smp_sketch_svd synchronises, so host wall time is its duration)
+    base = None
+    if rank == 0 and not args.no_baseline:
+        solver.sketch_svd(w["r"], seed=4)
+        reps = 3
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            Ub, Sb, Vb = solver.sketch_svd(w["r"], seed=4)
+        base = {"name": "SVD(A~^T B~) by block power iteration (smp_sketch_svd)",
+                "ms": 1e3 * (time.perf_counter() - t0) / reps, "spectral_err": None}
+
+    # the Appendix's row-wise multinomial sampler against the Bernoulli coins on the same sketches: sampling time
+    # (both synchronise: host wall time), |Omega|, and the error of a full WAltMin on the multinomial Omega
+    mn = None
+    if rank == 0 and not args.no_baseline:
+        def timed(fn, reps=3):
+            fn()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                out = fn()
+            return out, 1e3 * (time.perf_counter() - t0) / reps
+        nnz_b, ms_b = timed(lambda: solver.sample(m, 2 + rank))
+        nnz_m, ms_m = timed(lambda: solver.sample(m, 2 + rank, "multinomial"))
+        Um, Sm, Vm = solver.waltmin(solver.estimate(nnz_m), w["r"], w["T"], 0, 3 + rank)
+        mn = {"name": "row-wise multinomial sampling (smp_sample_multinomial)", "sample_ms": ms_m,
+              "bernoulli_sample_ms": ms_b, "nnz": int(nnz_m), "bernoulli_nnz": int(nnz_b), "spectral_err": None}
+
     err, opt_err = None, None
     if not args.no_error and rank == 0:
-        err, opt_err = spectral_error(torch, A, B, U, S, V)
+        extra = ([(Ub, Sb, Vb)] if base else []) + ([(Um, Sm, Vm)] if mn else [])
+        errs, opt_err = spectral_error(torch, A, B, [(U, S, V)] + extra)
+        err = errs[0]
+        if base:
+            base["spectral_err"] = errs[1]
+        if mn:
+            mn["spectral_err"] = errs[-1]
 
     # ---- end to end: host-resident inputs copied in every step (pinned, double-buffered row blocks)
     e2e = None
@@ -312,6 +349,7 @@ def main():
                 "p50_ms": statistics.median(step_ms), "p99_ms": step_ms[min(len(step_ms) - 1,
                                                                             int(math.ceil(0.99 * len(step_ms))) - 1)],
                 "sketch_gbs": roof["hbm_gbs"], "spectral_err": err, "optimal_err": opt_err,
+                "baseline_sketch_svd": base, "sampler_multinomial": mn,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk}
         print(json.dumps(line), flush=True)

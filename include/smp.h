@@ -139,6 +139,19 @@ smp_status smp_sketch_import(smp_ctx* ctx, const void* At_dev, const void* Bt_de
  * Errors: SMP_ESTATE (before finalize), SMP_EINVAL (m <= 0, both Frobenius norms zero), SMP_ENOMEM. */
 smp_status smp_sample(smp_ctx* ctx, double m, uint64_t seed, int64_t* nnz_out);
 
+/* Row-wise multinomial sampling of Omega (Appendix, "Sampling"), the alternative to smp_sample's Bernoulli coins.
+ * With alpha_i, beta_j of Eq. (1) as in smp_sample (unclipped q_ij = alpha_i + beta_j): Bcum = inclusive prefix sums
+ * of beta (1,024-element blocks summed left to right, each block offset by the left-to-right sum of the earlier
+ * blocks' totals); row i has S_i = n2 alpha_i + Bcum_{n2-1} (= the Appendix's m_i) and draws c_i = floor(S_i + 1/2)
+ * columns; draw s takes u = the 53-bit Philox uniform of counter (i, s, 0, 5) under key seed, t = u S_i, and the
+ * smallest j with t < (j + 1) alpha_i + Bcum_j (j = n2 - 1 if none), i.e. column j with probability q_ij / S_i.
+ * Omega is the set of distinct drawn pairs (CSR / CSC exactly as smp_sample builds them); the q^ stored with each
+ * pair is (c_i ((alpha_i + beta_j) / S_i)) / count_ij (count_ij = its draws), so smp_waltmin's weight 1/q^ is the
+ * unbiased importance weight. Every step is one round-to-nearest binary64 operation in the order written.
+ * Synchronises (twice: the draw total, then nnz). Errors: SMP_ESTATE (before finalize), SMP_EINVAL (m <= 0, both
+ * Frobenius norms zero), SMP_ENOMEM. */
+smp_status smp_sample_multinomial(smp_ctx* ctx, double m, uint64_t seed, int64_t* nnz);
+
 /* smp_sample with caller-supplied column sums of squares (double device arrays of n1 and n2 entries) in place of
  * the sketch's: the stage-parity hook for bit-exact Omega. Does not need a finalized sketch. */
 smp_status smp_sample_from_norms(smp_ctx* ctx, const double* sA_dev, const double* sB_dev, double m,
@@ -177,8 +190,9 @@ smp_status smp_waltmin(smp_ctx* ctx, const void* vals_dev, int32_t r, int32_t T,
  * min(2r + 8, 64, n1, n2, k) columns, Philox start block on the right (counter (j, 0, c/4, 4) under key seed),
  * orthonormalised by Cholesky-QR; each iteration Y = M Z, Y orthonormalised, Z = M^T Y. Every second (binary32
  * sketches) or fourth (binary64) iteration the top-r Ritz vectors U = Y E_r (E: eigenvectors of Z^T Z, binary64
- * Jacobi) are compared with the previous check's; the iteration stops when they move by less than 2e-5 (1e-11)
- * in sqrt(r - ||U^T U_prev||_F^2), or after 200 (400) iterations. Output: U = Y E_r, S = sqrt(eigenvalues),
+ * Jacobi) and their values (eigenvalues of Z^T Z) are compared with the previous check's; the iteration stops when
+ * the vectors move by less than 2e-5 (1e-11) in sqrt(r - ||U^T U_prev||_F^2), when no value changes by more than
+ * 2e-7 (1e-14) of the largest, or after 200 (400) iterations. Output: U = Y E_r, S = sqrt(eigenvalues),
  * V = Z E_r / S, the largest-magnitude entry of each U column made positive. Products in the sketch precision
  * (binary32 or binary64), reductions over the long dimension finished in binary64.
  * 1 <= r <= 32, r <= min(n1, n2, k). Outputs (device, double, row-major): U_dev n1 x r, S_dev r, V_dev n2 x r.

@@ -56,7 +56,7 @@ void free_ctx(smp_ctx* c) {
     release_tc(c);
     void* ptrs[] = {c->part,   c->nsq,    c->sk,      c->s_all,   c->D_all,   c->F,     c->row_ptr, c->col_ptr,
                     c->col,    c->qhat,   c->csc_row, c->csc_pos, c->alpha,   c->beta,  c->mask,    c->wpre,
-                    c->erow,
+                    c->erow,   c->mn_S,   c->mn_bcum, c->mn_btot, c->mn_rows, c->mn_off, c->mn_draw, c->mn_count,
                     c->row_cnt, c->col_cnt, c->dev_err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -257,6 +257,18 @@ smp_status smp_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out) {
     if (e != cudaSuccess) return check_cuda(c, e, "smp_sample");
     if (!(F[0] > 0.0) && !(F[1] > 0.0)) return fail(c, SMP_EINVAL, "both Frobenius norms are zero");
     return run_sample(c, m, seed, nnz_out);
+}
+
+smp_status smp_sample_multinomial(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out) {
+    if (!c) return fail(nullptr, SMP_EINVAL, "null context");
+    if (!c->finalized) return fail(c, SMP_ESTATE, "smp_sample_multinomial before finalize");
+    if (!(m > 0.0)) return fail(c, SMP_EINVAL, "m must be > 0");
+    double F[2];
+    cudaError_t e = cudaMemcpyAsync(F, c->F, 16, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return check_cuda(c, e, "smp_sample_multinomial");
+    if (!(F[0] > 0.0) && !(F[1] > 0.0)) return fail(c, SMP_EINVAL, "both Frobenius norms are zero");
+    return run_sample(c, m, seed, nnz_out, true);
 }
 
 smp_status smp_sample_from_norms(smp_ctx* c, const double* sA, const double* sB, double m, uint64_t seed,

@@ -42,6 +42,16 @@ struct smp_ctx {
     int32_t* row_cnt = nullptr;     // [n1]
     int32_t* col_cnt = nullptr;     // [n2]
     int64_t mask_words = 0;
+    // row-wise multinomial sampling (allocated on first use)
+    double* mn_S = nullptr;         // [n1] row totals S_i
+    double* mn_bcum = nullptr;      // [n2] blocked prefix sums of beta
+    double* mn_btot = nullptr;      // [ceil(n2 / 1024)] block totals, then block offsets
+    int32_t* mn_rows = nullptr;     // [n1] draws per row c_i
+    int64_t* mn_off = nullptr;      // [n1 + 1] first draw of each row
+    int32_t* mn_draw = nullptr;     // [mn_draw_cap] drawn column of every draw
+    int64_t mn_draw_cap = 0;
+    int32_t* mn_count = nullptr;    // [mn_count_cap] draws of each Omega entry (CSR order)
+    int64_t mn_count_cap = 0;
     int* dev_err = nullptr;         // device error word
     // tensor-core engine: two Pi buffers filled on a side stream; while one row block is sketched, Pi of the next
     // one (row0 + nrows, same size) is generated speculatively into the other buffer
@@ -120,7 +130,7 @@ cudaError_t launch_sketch_tc_pi(smp_ctx* c, const void* A, int64_t lda, const vo
                                 int64_t nrows, const float* Pi, int64_t ldp);
 
 // sample.cu
-smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out);
+smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out, bool multinomial = false);
 
 // estimate.cu
 cudaError_t launch_estimate(smp_ctx* c, void* vals);

@@ -1183,12 +1183,15 @@ smp_status sketch_svd_typed(smp_ctx* c, int r, uint64_t seed, double* U, double*
     // Philox start block on the right (TAG_INIT), orthonormalised
     start_block_kernel<TY><<<smp::counted(nblocks(n2 * ((b + 3) / 4), 256)), 256, 0, st>>>(n2, b, k0, k1, Z);
     cholqr2<TY, TY, TY>(Z, n2, b, Z, gpart, G, R1, R2, nullptr, st);
-    // Each iteration: Y = M Z, orthonormalise Y, Z = M^T Y. Every `every` iterations the top-r Ritz vectors
-    // Y E_r (E: eigenvectors of Z^T Z, binary64 Jacobi) are compared with those of the previous check; the
-    // iteration stops once they move by less than tol (sqrt(r - ||U0^T U0prev||_F^2)).
+    // Each iteration: Y = M Z, orthonormalise Y, Z = M^T Y. Every `every` iterations the top-r Ritz pairs are
+    // compared with those of the previous check (E: eigenvectors of Z^T Z, binary64 Jacobi; vectors Y E_r): the
+    // iteration stops once the vectors move by less than tol (sqrt(r - ||U^T Uprev||_F^2)) or the values
+    // lambda_1..r change by less than vtol lambda_1 (the values converge at twice the rate of the vectors and do
+    // not see rotations inside a cluster of nearly equal singular values, which leave the rank-r error unchanged).
     const bool dbl = sizeof(TY) == 8;
     const int max_iter = dbl ? 400 : 200, every = dbl ? 4 : 2;
-    const double tol = dbl ? 1e-11 : 2e-5;
+    const double tol = dbl ? 1e-11 : 2e-5, vtol = dbl ? 1e-14 : 2e-7;
+    std::vector<double> ev_prev(r, 0.0), ev_cur(r, 0.0);
     smp_status status = SMP_OK;
     bool have_prev = false;
     for (int it = 1; it <= max_iter; ++it) {
@@ -1208,17 +1211,23 @@ smp_status sketch_svd_typed(smp_ctx* c, int r, uint64_t seed, double* U, double*
             bool done = false;
             if (have_prev) {
                 gram<double, double>(U, U0p, n1, r, r, gpart, Gx, st);
-                std::vector<double> hx(r * r);
-                cudaError_t e1 = cudaMemcpyAsync(hx.data(), Gx, sizeof(double) * r * r, cudaMemcpyDeviceToHost, st);
-                if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(st);
-                if (e1 != cudaSuccess) {
-                    status = check_cuda(c, e1, "smp_sketch_svd check");
-                    break;
-                }
-                double fro = 0.0;
-                for (double v : hx) fro += v * v;
-                done = std::sqrt(std::max(0.0, (double)r - fro)) < tol;
             }
+            std::vector<double> hx(r * r);
+            cudaError_t e1 = cudaMemcpyAsync(ev_cur.data(), ev, sizeof(double) * r, cudaMemcpyDeviceToHost, st);
+            if (e1 == cudaSuccess && have_prev)
+                e1 = cudaMemcpyAsync(hx.data(), Gx, sizeof(double) * r * r, cudaMemcpyDeviceToHost, st);
+            if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(st);
+            if (e1 != cudaSuccess) {
+                status = check_cuda(c, e1, "smp_sketch_svd check");
+                break;
+            }
+            if (have_prev) {
+                double fro = 0.0, dv = 0.0;
+                for (double v : hx) fro += v * v;
+                for (int i = 0; i < r; ++i) dv = std::max(dv, std::fabs(ev_cur[i] - ev_prev[i]));
+                done = std::sqrt(std::max(0.0, (double)r - fro)) < tol || dv < vtol * std::fabs(ev_cur[0]);
+            }
+            ev_prev = ev_cur;
             have_prev = true;
             if (done || it == max_iter) {
                 // M ~ Y Y^T M = Y Z^T = (Y E)(Z E)^T, and Z E has orthogonal columns of norms sqrt(lambda)

@@ -50,7 +50,10 @@ class Solver:
             S.smp_sketch_accumulate(self.ctx, a, A.stride(0), b, 0 if b is None else B.stride(0), r0, r1 - r0)
         S.smp_sketch_finalize(self.ctx)
 
-    def sample(self, m, seed=2):
+    def sample(self, m, seed=2, sampler="bernoulli"):
+        """Omega by the Bernoulli coins of Eq. (1) (smp_sample) or row-wise multinomial draws (Appendix)."""
+        if sampler == "multinomial":
+            return S.smp_sample_multinomial(self.ctx, m, seed)
         return S.smp_sample(self.ctx, m, seed)
 
     def estimate(self, nnz):
@@ -73,10 +76,10 @@ class Solver:
         S.smp_sketch_svd(self.ctx, r, seed, U, Sv, V)
         return U, Sv, V
 
-    def solve(self, A, B, r, T, m=None, sample_seed=2, walt_seed=3, flags=0, block_rows=65536):
+    def solve(self, A, B, r, T, m=None, sample_seed=2, walt_seed=3, flags=0, block_rows=65536, sampler="bernoulli"):
         m = default_m(self.n1, self.n2, r) if m is None else m
         self.sketch(A, B, block_rows)
-        nnz = self.sample(m, sample_seed)
+        nnz = self.sample(m, sample_seed, sampler)
         vals = self.estimate(nnz)
         U, Sv, V = self.waltmin(vals, r, T, flags, walt_seed)
         return dict(U=U, S=Sv, V=V, nnz=nnz, vals=vals)

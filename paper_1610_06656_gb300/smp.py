@@ -37,6 +37,7 @@ SIGNATURES = {
                                _c.POINTER(_vp), _c.POINTER(_f64)]),
     "smp_sketch_import": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "smp_sample": (_i32, [_vp, _f64, _u64, _c.POINTER(_i64)]),
+    "smp_sample_multinomial": (_i32, [_vp, _f64, _u64, _c.POINTER(_i64)]),
     "smp_sample_from_norms": (_i32, [_vp, _vp, _vp, _f64, _u64, _c.POINTER(_i64)]),
     "smp_omega_view": (_i32, [_vp, _c.POINTER(_i64), _c.POINTER(_vp), _c.POINTER(_vp), _c.POINTER(_vp),
                               _c.POINTER(_vp), _c.POINTER(_vp), _c.POINTER(_vp)]),
@@ -151,6 +152,13 @@ def smp_sketch_import(ctx, At, Bt, sA, sB):
 def smp_sample(ctx, m, seed):
     nnz = _i64()
     _check(load().smp_sample(ctx, float(m), seed & 0xFFFFFFFFFFFFFFFF, _c.byref(nnz)), "smp_sample", ctx)
+    return nnz.value
+
+
+def smp_sample_multinomial(ctx, m, seed):
+    nnz = _i64()
+    _check(load().smp_sample_multinomial(ctx, float(m), seed & 0xFFFFFFFFFFFFFFFF, _c.byref(nnz)),
+           "smp_sample_multinomial", ctx)
     return nnz.value
 
 
