@@ -22,6 +22,9 @@ The paper being implemented only asks for Pi(i, j) ~ N(0, 1/k) i.i.d. (Algorithm
   split coin     : counter = (i, j, 0, TAG_SPLIT), same 53-bit mapping
   init block     : counter = (i, 0, c // 4, TAG_INIT), same Gaussian mapping as Pi (no 1/sqrt(k))
   multinomial    : counter = (i, s, 0, TAG_MULTI) for draw s of row i, same 53-bit mapping as the coins
+  SRHT sign      : counter = (t mod 2^32, t >> 32, 0, TAG_SRHT_SIGN); D_tt = -1 iff bit 0 of x0 is set
+  SRHT row       : counter = (a, b mod 2^32, b >> 32, TAG_SRHT_ROW); row a of block b samples Hadamard row
+                   x0 >> (32 - p) of the 2^p-row block
 
 Both uniforms are exact in binary32 and binary64, so the two sides see identical uniforms; they differ only in
 how ln / sqrt / cos / sin are rounded.
@@ -41,6 +44,8 @@ TAG_SAMPLE = 2
 TAG_SPLIT = 3
 TAG_INIT = 4
 TAG_MULTI = 5
+TAG_SRHT_SIGN = 6
+TAG_SRHT_ROW = 7
 
 TWO_M24 = 2.0 ** -24
 TWO_M53 = 2.0 ** -53

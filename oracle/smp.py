@@ -55,6 +55,74 @@ class SketchState:
         self.rows_seen += R
 
 
+def fwht(X):
+    """Unnormalised fast Walsh-Hadamard transform along axis 0 (length a power of two), Sylvester order:
+    Y[s] = sum_t (-1)^popcount(s & t) X[t]. Butterflies of span 1, 2, 4, ... in binary64."""
+    Y = np.array(X, dtype=np.float64, copy=True)
+    n = Y.shape[0]
+    h = 1
+    while h < n:
+        Y = Y.reshape((n // (2 * h), 2, h) + Y.shape[1:])
+        a = Y[:, 0].copy()
+        Y[:, 0] = a + Y[:, 1]
+        Y[:, 1] = a - Y[:, 1]
+        Y = Y.reshape((n,) + Y.shape[3:])
+        h *= 2
+    return Y
+
+
+def srht_signs(seed, t0, nrows):
+    """D_tt = +-1 for data rows t0 .. t0 + nrows - 1 (bit 0 of the Philox word x0 set: -1)."""
+    k0, k1 = philox.seed_key(seed)
+    t = np.arange(t0, t0 + nrows, dtype=np.uint64)
+    x0, _, _, _ = philox.philox4x32_10(t & np.uint64(philox.MASK32), t >> np.uint64(32), np.uint64(0),
+                                       np.uint64(philox.TAG_SRHT_SIGN), k0, k1)
+    return np.where((x0 & np.uint64(1)) != 0, -1.0, 1.0)
+
+
+def srht_rows(seed, b, k, p):
+    """The k Hadamard rows block b samples (uniformly, with replacement): the top p bits of x0."""
+    k0, k1 = philox.seed_key(seed)
+    a = np.arange(k, dtype=np.uint64)
+    x0, _, _, _ = philox.philox4x32_10(a, np.uint64(b & philox.MASK32), np.uint64(b >> 32),
+                                       np.uint64(philox.TAG_SRHT_ROW), k0, k1)
+    return (x0 >> np.uint64(32 - p)).astype(np.int64)
+
+
+def sketch_srht(A, B, k, seed, block_log2, same_ab=False):
+    """Step 1 with a block subsampled randomized Hadamard transform as Pi (Section 4: the Spark implementation's
+    sketch; its footnote: O(nd log d) time and O(d) space instead of O(ndk) and O(dk)).
+
+    Reading (the paper cites the SRHT without a streaming form): the data rows are cut into blocks of R = 2^p rows
+    (block b = rows [bR, (b+1)R), the last one zero-padded) and Pi = [Pi_0, Pi_1, ...] with independent
+    Pi_b = k^-1/2 S_b H_R D_b: D_b the random signs of srht_signs, H_R the unnormalised Walsh-Hadamard matrix, S_b
+    k rows of H_R drawn uniformly with replacement (srht_rows); E[Pi^T Pi] = I. So
+    At = sum_b k^-1/2 (H_R D_b A_b)[S_b, :], each block through fwht. Norms as in sketch(). Returns a SketchState.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    d, n1 = A.shape
+    B = A if same_ab else np.asarray(B, dtype=np.float64)
+    n2 = B.shape[1]
+    R = 1 << block_log2
+    st = SketchState(n1, n2, k, seed, same_ab)
+    inv = 1.0 / np.sqrt(float(k))
+    for b, t0 in enumerate(range(0, d, R)):
+        rows = min(R, d - t0)
+        D = srht_signs(seed, t0, rows)[:, None]
+        S = srht_rows(seed, b, k, block_log2)
+        XA = np.zeros((R, n1))
+        XA[:rows] = D * A[t0:t0 + rows]
+        st.At += inv * fwht(XA)[S]
+        st.sA += np.sum(A[t0:t0 + rows] ** 2, axis=0)
+        if not same_ab:
+            XB = np.zeros((R, n2))
+            XB[:rows] = D * B[t0:t0 + rows]
+            st.Bt += inv * fwht(XB)[S]
+            st.sB += np.sum(B[t0:t0 + rows] ** 2, axis=0)
+        st.rows_seen += rows
+    return st
+
+
 def frobenius_sq(s):
     """||A||_F^2 = sum_i ||A_i||^2, summed strictly left to right (the order the sampler's reading fixes)."""
     total = 0.0
@@ -370,10 +438,14 @@ def default_m(n1, n2, r):
 
 
 def smp_pca(A, B, r, k, m, T, seed, sample_seed, block_rows=65536, same_ab=False, split=SPLIT_NONE,
-            split_seed=0, pi=None, sampler="bernoulli"):
+            split_seed=0, pi=None, sampler="bernoulli", srht_log2=None):
     """Algorithm 1 end to end. Returns a dict with every intermediate and the canonical (U, S, V). sampler:
-    "bernoulli" (Eq. (1) coins, step 3) or "multinomial" (the Appendix's row-wise sampling)."""
-    st = sketch(A, B, k, seed, block_rows, same_ab, pi)
+    "bernoulli" (Eq. (1) coins, step 3) or "multinomial" (the Appendix's row-wise sampling). srht_log2: sketch
+    with the block SRHT of 2^srht_log2-row blocks instead of the Gaussian Pi."""
+    if srht_log2 is not None:
+        st = sketch_srht(A, B, k, seed, srht_log2, same_ab)
+    else:
+        st = sketch(A, B, k, seed, block_rows, same_ab, pi)
     if sampler == "multinomial":
         rows, cols, qhat, _ = sample_omega_multinomial(st.sA, st.sB, m, sample_seed)
     else:
