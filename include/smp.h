@@ -57,10 +57,18 @@ typedef enum {
     SMP_ENGINE_TC = 2,     /* tcgen05 sketch, FP32 accumulation: SMP_F32 as TF32 operands with k <= 512 (row
                               blocks 16-byte aligned, lda, ldb multiples of 4); SMP_BF16 as BF16 operands with
                               k <= 1024 (row blocks 16-byte aligned, lda, ldb multiples of 8) */
-    SMP_ENGINE_TC_FP8 = 3  /* tcgen05 sketch of SMP_BF16 row blocks with FP8 E4M3 operands: each block is scaled by
+    SMP_ENGINE_TC_FP8 = 3, /* tcgen05 sketch of SMP_BF16 row blocks with FP8 E4M3 operands: each block is scaled by
                               one power of two per matrix, 2^ceil(log2(max |x| / 448)), Pi is E4M3 of the normals,
                               FP32 accumulation; column norms of the stored BF16 values. k <= 1024, alignment as for
                               SMP_BF16. Never chosen by SMP_ENGINE_AUTO. */
+    SMP_ENGINE_SRHT = 4    /* block SRHT as Pi (Section 4: the Spark implementation's sketch) instead of the Gaussian:
+                              data rows in blocks of R = max_rows rows (a power of two in [256, 2^16]; block b =
+                              rows [bR, (b+1)R)), Pi_b = k^-1/2 S_b H_R D_b with D_b the signs of Philox counter
+                              (t mod 2^32, t >> 32, 0, 6) (bit 0 of word 0 set: -1), H_R the unnormalised Sylvester
+                              Walsh-Hadamard matrix and S_b k rows of H_R drawn with replacement (row a: the top
+                              log2(R) bits of word 0 of counter (a, b mod 2^32, b >> 32, 7)). SMP_F32 only; every
+                              accumulate call covers one block (row0 % max_rows == 0); binary32 arithmetic, norms
+                              compensated as in the other engines. Never chosen by SMP_ENGINE_AUTO. */
 } smp_engine;
 
 /* smp_waltmin flags */

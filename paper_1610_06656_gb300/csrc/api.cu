@@ -56,7 +56,7 @@ void free_ctx(smp_ctx* c) {
     release_tc(c);
     void* ptrs[] = {c->part,   c->nsq,    c->sk,      c->s_all,   c->D_all,   c->F,     c->row_ptr, c->col_ptr,
                     c->col,    c->qhat,   c->csc_row, c->csc_pos, c->alpha,   c->beta,  c->mask,    c->wpre,
-                    c->erow,   c->mn_S,   c->mn_bcum, c->mn_btot, c->mn_rows, c->mn_off, c->mn_draw, c->mn_count,
+                    c->erow,   c->srht_y, c->srht_nsq, c->srht_rows, c->mn_S,   c->mn_bcum, c->mn_btot, c->mn_rows, c->mn_off, c->mn_draw, c->mn_count,
                     c->row_cnt, c->col_cnt, c->dev_err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -96,7 +96,13 @@ smp_status smp_sketch_begin(const smp_params* params, void* stream, smp_ctx** ou
         return fail(nullptr, SMP_EINVAL, "n1, n2 must be in [1, 2^30]");
     if (p.same_ab && p.n1 != p.n2) return fail(nullptr, SMP_EINVAL, "same_ab needs n1 == n2");
     if (p.k < 1 || p.k > 1024) return fail(nullptr, SMP_EINVAL, "k must be in [1, 1024]");
-    if (p.engine < SMP_ENGINE_AUTO || p.engine > SMP_ENGINE_TC_FP8) return fail(nullptr, SMP_EINVAL, "unknown engine");
+    if (p.engine < SMP_ENGINE_AUTO || p.engine > SMP_ENGINE_SRHT) return fail(nullptr, SMP_EINVAL, "unknown engine");
+    if (p.engine == SMP_ENGINE_SRHT) {
+        if (p.dtype != SMP_F32) return fail(nullptr, SMP_EUNSUPPORTED, "SMP_ENGINE_SRHT takes SMP_F32 row blocks");
+        const int64_t R = p.max_rows ? p.max_rows : 65536;
+        if (R < 256 || R > 65536 || (R & (R - 1)) != 0)
+            return fail(nullptr, SMP_EINVAL, "SMP_ENGINE_SRHT needs max_rows a power of two in [256, 65536]");
+    }
     if (p.engine == SMP_ENGINE_TC_FP8 && p.dtype != SMP_BF16)
         return fail(nullptr, SMP_EUNSUPPORTED, "SMP_ENGINE_TC_FP8 takes SMP_BF16 row blocks");
     if (p.max_rows < 0) return fail(nullptr, SMP_EINVAL, "max_rows < 0");
@@ -164,6 +170,11 @@ smp_status smp_sketch_accumulate(smp_ctx* c, const void* A, int64_t lda, const v
             return fail(c, SMP_EUNSUPPORTED, "the FP8 sketch needs k <= 1024, 16-byte aligned blocks, lda, ldb % 8 == 0");
         return check_cuda(c, launch_sketch_fp8(c, A, lda, B, ldb, row0, nrows, nullptr, 0), "smp_sketch_accumulate");
     }
+    if (c->p.engine == SMP_ENGINE_SRHT) {
+        if (!srht_block_ok(c, row0, nrows))
+            return fail(c, SMP_EINVAL, "the SRHT sketch takes whole blocks: row0 % max_rows == 0");
+        return check_cuda(c, launch_sketch_srht(c, A, lda, B, ldb, row0, nrows), "smp_sketch_accumulate");
+    }
     const bool bf16 = c->p.dtype == SMP_BF16;
     const bool tc_ok = bf16 ? bf16_block_ok(c, A, lda, B, ldb) : tc_block_ok(c, A, lda, B, ldb);
     if (c->p.engine == SMP_ENGINE_TC && !tc_ok)
@@ -182,6 +193,7 @@ smp_status smp_sketch_accumulate_pi(smp_ctx* c, const void* Pi, int64_t ldp, con
     smp_status s = check_block(c, A, lda, B, ldb, nrows);
     if (s != SMP_OK || nrows == 0) return s;
     if (!Pi || ldp < nrows) return fail(c, SMP_EINVAL, "Pi_blk is null or ldp < nrows");
+    if (c->p.engine == SMP_ENGINE_SRHT) return fail(c, SMP_EUNSUPPORTED, "the SRHT engine generates its own Pi");
     if (c->p.engine == SMP_ENGINE_TC_FP8) {
         if (!fp8_block_ok(c, A, lda, B, ldb))
             return fail(c, SMP_EUNSUPPORTED, "the FP8 sketch needs k <= 1024, 16-byte aligned blocks, lda, ldb % 8 == 0");

@@ -15,7 +15,15 @@ enum : int {
 };
 
 // Philox counter tags (fourth counter word) of the four random streams.
-enum : uint32_t { TAG_PI = 1u, TAG_SAMPLE = 2u, TAG_SPLIT = 3u, TAG_INIT = 4u, TAG_MULTI = 5u };
+enum : uint32_t {
+    TAG_PI = 1u,
+    TAG_SAMPLE = 2u,
+    TAG_SPLIT = 3u,
+    TAG_INIT = 4u,
+    TAG_MULTI = 5u,
+    TAG_SRHT_SIGN = 6u,
+    TAG_SRHT_ROW = 7u
+};
 
 struct U32x4 {
     uint32_t x, y, z, w;

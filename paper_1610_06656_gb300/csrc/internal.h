@@ -51,6 +51,10 @@ struct smp_ctx {
     int32_t* mn_draw = nullptr;     // [mn_draw_cap] drawn column of every draw
     int64_t mn_draw_cap = 0;
     int32_t* mn_count = nullptr;    // [mn_count_cap] draws of each Omega entry (CSR order)
+    // block SRHT sketch (allocated on first use)
+    float* srht_y = nullptr;        // [max_rows][256] chunk transforms of one column group
+    double* srht_nsq = nullptr;     // [max_rows / 256][256] chunk column sums of squares
+    int32_t* srht_rows = nullptr;   // bucket offsets [257], bucketed sketch rows [1024], s >> 8 per row [1024]
     int64_t mn_count_cap = 0;
     int* dev_err = nullptr;         // device error word
     // tensor-core engine: two Pi buffers filled on a side stream; while one row block is sketched, Pi of the next
@@ -112,6 +116,11 @@ cudaError_t pi_release(smp_ctx* c, int b, int64_t row0, int64_t nrows);
 // A caller's Pi (k x nrows binary32, row stride ldp) rounded into a Pi buffer (BF16 contexts); the buffer is then
 // released with pi_release like a generated one.
 cudaError_t pi_import(smp_ctx* c, const float* Pi, int64_t ldp, int64_t nrows, int* buf);
+
+// sketch_srht.cu
+bool srht_block_ok(const smp_ctx* c, int64_t row0, int64_t nrows);
+cudaError_t launch_sketch_srht(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t row0,
+                               int64_t nrows);
 
 // sketch_fp8.cu
 bool fp8_block_ok(const smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb);
