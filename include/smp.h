@@ -42,7 +42,8 @@ typedef enum {
     SMP_ESTATE = 4,        /* call out of order (e.g. accumulate after finalize, estimate before sample) */
     SMP_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
     SMP_ENUMERIC = 6,      /* a factorisation broke down (non-positive pivot) */
-    SMP_EUNSUPPORTED = 7   /* valid request this build does not implement (e.g. dtype/engine pair) */
+    SMP_EUNSUPPORTED = 7,  /* valid request this build does not implement (e.g. dtype/engine pair) */
+    SMP_EBUSY = 8          /* serving: the job does not fit in what is left of the memory budget; retry later */
 } smp_status;
 
 typedef enum {
@@ -206,6 +207,70 @@ smp_status smp_waltmin(smp_ctx* ctx, const void* vals_dev, int32_t r, int32_t T,
  * 1 <= r <= 32, r <= min(n1, n2, k). Outputs (device, double, row-major): U_dev n1 x r, S_dev r, V_dev n2 x r.
  * Synchronises. Errors: SMP_ESTATE (sketch not finalized), SMP_EINVAL, SMP_ENOMEM. */
 smp_status smp_sketch_svd(smp_ctx* ctx, int32_t r, uint64_t seed, double* U_dev, double* S_dev, double* V_dev);
+
+/* ---------------------------------------------------------------------------------------------------------------
+ * Serving form: a request loop with continuous batching. Each admitted job owns a context (resident sketch state,
+ * Omega, scratch) on a CUDA stream of its own; row blocks of many jobs arrive interleaved and sketch concurrently;
+ * when a job is closed, one of solve_workers host threads runs finalize, sample (Bernoulli, Eq. (1)), estimate and
+ * WAltMin for it on its stream while other jobs keep sketching. Admission is gated by a device-memory budget:
+ * a job is admitted only if smp_serve_job_bytes of it fits in the budget left, else SMP_EBUSY. A job's results do
+ * not depend on what else runs (its kernels touch only its context; every reduction has a fixed order).
+ * Threading: admit / block / close for one job come from one host thread at a time; collect, poll, cancel and
+ * stats may come from any thread. The caller keeps each pushed block's memory valid until the job is collected
+ * or cancelled.
+ * ------------------------------------------------------------------------------------------------------------- */
+typedef struct smp_server smp_server;
+
+typedef struct {
+    int64_t hbm_budget_bytes;   /* device memory the admitted jobs may hold together (> 0)                       */
+    int32_t solve_workers;      /* host threads running the solve chain of closed jobs, 1..64                     */
+} smp_server_params;
+
+typedef struct {
+    smp_params sketch;          /* the job's sketch context (smp_sketch_begin), stream chosen by the server        */
+    int32_t r, T;               /* rank and WAltMin iterations (smp_waltmin)                                      */
+    uint32_t flags;             /* smp_waltmin flags                                                              */
+    double m;                   /* expected samples (smp_sample)                                                  */
+    uint64_t sample_seed, walt_seed;
+} smp_job_params;
+
+/* Upper bound on the device bytes a job's context, Omega, scratch and results can hold (the admission charge).
+ * Host only. Errors: SMP_EINVAL. */
+smp_status smp_serve_job_bytes(const smp_job_params* job, int64_t* bytes);
+
+/* Start a server on the current device with its worker threads. Errors: SMP_EINVAL, SMP_ENOMEM, SMP_ECUDA. */
+smp_status smp_serve_create(const smp_server_params* params, smp_server** out);
+
+/* Admit a job: reserve its bytes, create its stream and context. *job_id identifies it until collected or
+ * cancelled. Errors: SMP_EBUSY (over budget), SMP_EINVAL, SMP_ENOMEM, SMP_ECUDA, SMP_ESTATE (server stopping). */
+smp_status smp_serve_admit(smp_server* server, const smp_job_params* job, int64_t* job_id);
+
+/* Sketch one row block of a streaming job (smp_sketch_accumulate on its context and stream). Asynchronous.
+ * Errors: as smp_sketch_accumulate; SMP_EINVAL (unknown job), SMP_ESTATE (job already closed). */
+smp_status smp_serve_block(smp_server* server, int64_t job_id, const void* A_blk_dev, int64_t lda,
+                           const void* B_blk_dev, int64_t ldb, int64_t row0, int64_t nrows);
+
+/* The job's last block has been pushed: queue its solve chain; its latency clock starts here. */
+smp_status smp_serve_close(smp_server* server, int64_t job_id);
+
+/* *done = 1 once the job's solve chain has finished (successfully or not). */
+smp_status smp_serve_poll(smp_server* server, int64_t job_id, int32_t* done);
+
+/* Wait for a closed job (timeout_s < 0: no limit; SMP_ETIMEOUT when it runs out, the job stays), copy its factors
+ * (U n1 x r, S r, V n2 x r, binary64, canonical form as smp_waltmin) to the caller's device buffers (any may be
+ * NULL), report |Omega| and the latency from close to the end of WAltMin, and release the job and its budget.
+ * Returns the job's own status when its chain failed. */
+smp_status smp_serve_collect(smp_server* server, int64_t job_id, double timeout_s, double* U_dev, double* S_dev,
+                             double* V_dev, int64_t* nnz, double* latency_ms);
+
+/* Drop a job in any state (a running solve is allowed to finish first) and release its budget. */
+smp_status smp_serve_cancel(smp_server* server, int64_t job_id);
+
+/* Bytes currently charged to admitted jobs and their number. */
+smp_status smp_serve_stats(smp_server* server, int64_t* used_bytes, int32_t* live_jobs);
+
+/* Stop the workers (queued jobs are not solved), release every job, free the server. NULL is a no-op. */
+smp_status smp_serve_destroy(smp_server* server);
 
 /* Block until the context's stream is idle and report any device-side error word. */
 smp_status smp_sync(smp_ctx* ctx);

@@ -370,6 +370,7 @@ const char* smp_status_string(smp_status s) {
         case SMP_ETIMEOUT: return "SMP_ETIMEOUT";
         case SMP_ENUMERIC: return "SMP_ENUMERIC";
         case SMP_EUNSUPPORTED: return "SMP_EUNSUPPORTED";
+        case SMP_EBUSY: return "SMP_EBUSY";
     }
     return "SMP_UNKNOWN";
 }

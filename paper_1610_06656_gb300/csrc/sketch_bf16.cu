@@ -342,7 +342,7 @@ bool bf16_block_ok(const smp_ctx* c, const void* A, int64_t lda, const void* B, 
 
 cudaError_t launch_sketch_bf16(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t row0,
                                int64_t nrows, const float* Pi, int64_t ldp) {
-    static bool attr = false;
+    static std::atomic<bool> attr{false};
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(sketch_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              SMEM_BYTES);

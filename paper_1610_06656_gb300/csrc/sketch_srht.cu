@@ -226,7 +226,7 @@ cudaError_t launch_sketch_srht(smp_ctx* c, const void* A, int64_t lda, const voi
         if (e == cudaSuccess) e = cudaMalloc((void**)&c->srht_nsq, (size_t)(R / SR_CHUNK) * SR_GROUP * 8);
         if (e == cudaSuccess) e = cudaMalloc((void**)&c->srht_rows, (size_t)(257 + 2 * 1024) * 4);
         if (e != cudaSuccess) return e;
-        static bool attr = false;
+        static std::atomic<bool> attr{false};
         if (!attr) {
             e = cudaFuncSetAttribute(srht_stage_a_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      SR_CHUNK * SR_COLS * 4);

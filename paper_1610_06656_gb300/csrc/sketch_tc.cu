@@ -570,7 +570,7 @@ bool tc_block_ok(const smp_ctx* c, const void* A, int64_t lda, const void* B, in
 
 cudaError_t launch_sketch_tc_pi(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t row0,
                                 int64_t nrows, const float* Pi, int64_t ldp) {
-    static bool attr = false;
+    static std::atomic<bool> attr{false};
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
         if (e != cudaSuccess) return e;

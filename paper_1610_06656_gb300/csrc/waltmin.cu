@@ -640,7 +640,7 @@ void cholqr2(const TX* X, int64_t n, int b, TQ* Q, double* part, double* G, doub
 
 // The Jacobi eigen kernel takes up to 2 MAX_SMALL (MAX_SMALL + 1) elements of dynamic shared memory.
 void jacobi_smem_attr() {
-    static bool done = false;
+    static std::atomic<bool> done{false};
     if (done) return;
     cudaFuncSetAttribute(jacobi_eig_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          2 * MAX_SMALL * (MAX_SMALL + 1) * 8);
@@ -755,7 +755,7 @@ void launch_ls(int r, const Segments& sg, const int32_t* idx, const int64_t* pos
     const unsigned g = nblocks(sg.nseg, LS_WARPS);
     const unsigned gr = nblocks(n_out * 32, 256);
     const unsigned gs = nblocks(n_out, 32);
-    static bool attr = false;
+    static std::atomic<bool> attr{false};
     if (!attr) {
         cudaFuncSetAttribute(solve_kernel<TF, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, solve_smem_bytes<32>());
         attr = true;

@@ -11,7 +11,7 @@ import os
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libsmp.so")
 
-SMP_OK, SMP_EINVAL, SMP_ENOMEM, SMP_ECUDA, SMP_ESTATE, SMP_ETIMEOUT, SMP_ENUMERIC, SMP_EUNSUPPORTED = range(8)
+SMP_OK, SMP_EINVAL, SMP_ENOMEM, SMP_ECUDA, SMP_ESTATE, SMP_ETIMEOUT, SMP_ENUMERIC, SMP_EUNSUPPORTED, SMP_EBUSY = range(9)
 SMP_F32, SMP_BF16, SMP_F64 = 0, 1, 2
 SMP_ENGINE_AUTO, SMP_ENGINE_SIMT, SMP_ENGINE_TC, SMP_ENGINE_TC_FP8, SMP_ENGINE_SRHT = 0, 1, 2, 3, 4
 SMP_SPLIT_OMEGA, SMP_NO_TRIM, SMP_INIT_GIVEN, SMP_FP64_ALS = 1, 2, 4, 8
@@ -26,8 +26,27 @@ class smp_params(_c.Structure):
                 ("engine", _i32), ("max_rows", _i64)]
 
 
+class smp_server_params(_c.Structure):
+    _fields_ = [("hbm_budget_bytes", _i64), ("solve_workers", _i32)]
+
+
+class smp_job_params(_c.Structure):
+    _fields_ = [("sketch", smp_params), ("r", _i32), ("T", _i32), ("flags", _u32), ("m", _f64),
+                ("sample_seed", _u64), ("walt_seed", _u64)]
+
+
 # name -> (restype, argtypes), mirroring include/smp.h
 SIGNATURES = {
+    "smp_serve_job_bytes": (_i32, [_c.POINTER(smp_job_params), _c.POINTER(_i64)]),
+    "smp_serve_create": (_i32, [_c.POINTER(smp_server_params), _c.POINTER(_vp)]),
+    "smp_serve_admit": (_i32, [_vp, _c.POINTER(smp_job_params), _c.POINTER(_i64)]),
+    "smp_serve_block": (_i32, [_vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64]),
+    "smp_serve_close": (_i32, [_vp, _i64]),
+    "smp_serve_poll": (_i32, [_vp, _i64, _c.POINTER(_i32)]),
+    "smp_serve_collect": (_i32, [_vp, _i64, _f64, _vp, _vp, _vp, _c.POINTER(_i64), _c.POINTER(_f64)]),
+    "smp_serve_cancel": (_i32, [_vp, _i64]),
+    "smp_serve_stats": (_i32, [_vp, _c.POINTER(_i64), _c.POINTER(_i32)]),
+    "smp_serve_destroy": (_i32, [_vp]),
     "smp_sketch_begin": (_i32, [_c.POINTER(smp_params), _vp, _c.POINTER(_vp)]),
     "smp_sketch_accumulate": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _i64]),
     "smp_sketch_accumulate_pi": (_i32, [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64]),
@@ -219,3 +238,71 @@ def smp_sketch_noalloc(A, lda, B, ldb, n1, n2, k, dtype, seed, row0, nrows, At, 
 
 def smp_launch_count():
     return load().smp_launch_count()
+
+
+# ------------------------------------------------------------------------------------------------ serving form
+def job_params(n1, n2, k, r, T, m, seed, sample_seed, walt_seed, dtype=SMP_F32, same_ab=False,
+               engine=SMP_ENGINE_AUTO, max_rows=0, flags=0):
+    sk = smp_params(n1=n1, n2=n2, k=k, dtype=dtype, seed=seed & 0xFFFFFFFFFFFFFFFF, same_ab=int(bool(same_ab)),
+                    engine=engine, max_rows=max_rows)
+    return smp_job_params(sketch=sk, r=r, T=T, flags=flags, m=float(m), sample_seed=sample_seed & 0xFFFFFFFFFFFFFFFF,
+                          walt_seed=walt_seed & 0xFFFFFFFFFFFFFFFF)
+
+
+def smp_serve_job_bytes(jp):
+    b = _i64()
+    _check(load().smp_serve_job_bytes(_c.byref(jp), _c.byref(b)), "smp_serve_job_bytes")
+    return b.value
+
+
+def smp_serve_create(hbm_budget_bytes, solve_workers=4):
+    p = smp_server_params(hbm_budget_bytes=int(hbm_budget_bytes), solve_workers=solve_workers)
+    out = _vp()
+    _check(load().smp_serve_create(_c.byref(p), _c.byref(out)), "smp_serve_create")
+    return out.value
+
+
+def smp_serve_admit(server, jp):
+    """Job id, or None when the budget is full (SMP_EBUSY)."""
+    jid = _i64()
+    st = load().smp_serve_admit(server, _c.byref(jp), _c.byref(jid))
+    if st == SMP_EBUSY:
+        return None
+    _check(st, "smp_serve_admit")
+    return jid.value
+
+
+def smp_serve_block(server, job, A_blk, lda, B_blk, ldb, row0, nrows):
+    _check(load().smp_serve_block(server, job, _ptr(A_blk), lda, _ptr(B_blk), ldb, row0, nrows), "smp_serve_block")
+
+
+def smp_serve_close(server, job):
+    _check(load().smp_serve_close(server, job), "smp_serve_close")
+
+
+def smp_serve_poll(server, job):
+    d = _i32()
+    _check(load().smp_serve_poll(server, job, _c.byref(d)), "smp_serve_poll")
+    return bool(d.value)
+
+
+def smp_serve_collect(server, job, U=None, S=None, V=None, timeout_s=-1.0):
+    """(nnz, latency_ms) after copying the factors into U, S, V (device tensors or None)."""
+    nnz, lat = _i64(), _f64()
+    _check(load().smp_serve_collect(server, job, float(timeout_s), _ptr(U), _ptr(S), _ptr(V), _c.byref(nnz),
+                                    _c.byref(lat)), "smp_serve_collect")
+    return nnz.value, lat.value
+
+
+def smp_serve_cancel(server, job):
+    _check(load().smp_serve_cancel(server, job), "smp_serve_cancel")
+
+
+def smp_serve_stats(server):
+    used, live = _i64(), _i32()
+    _check(load().smp_serve_stats(server, _c.byref(used), _c.byref(live)), "smp_serve_stats")
+    return used.value, live.value
+
+
+def smp_serve_destroy(server):
+    _check(load().smp_serve_destroy(server), "smp_serve_destroy")

@@ -1,0 +1,113 @@
+"""The serving form on the GPU: a job's factors are the same bits alone, in a mix of interleaved jobs and through
+the plain pipeline; admission by budget, cancellation and collection."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1610_06656_gb300 import serve, synth
+from tests.gpu_helpers import build_lib, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch_cuda()
+    smp = build_lib()
+    from paper_1610_06656_gb300 import pipeline
+    A, B, _, _, _ = synth.lowrank_plus_noise_torch(300_000, 512, 512, 20, 0.1, 0.5, seed=1004, device="cuda",
+                                                   dtype=torch.bfloat16)
+    return smp, pipeline, A.contiguous(), B.contiguous()
+
+
+def _factors(n, r):
+    return (torch.empty(n, r, dtype=torch.float64, device="cuda"), torch.empty(r, dtype=torch.float64, device="cuda"),
+            torch.empty(n, r, dtype=torch.float64, device="cuda"))
+
+
+def _jobs(count, seed):
+    return serve.poisson_jobs(count, 2000.0, seed, pool_rows=300_000, n_range=(64, 512), d_range=(10_000, 120_000))
+
+
+def test_alone_mixed_and_plain_agree(env):
+    smp, pipeline, A, B = env
+    jobs = _jobs(12, seed=7)
+    probe = jobs[5]
+    sv = smp.smp_serve_create(8 << 30, solve_workers=3)
+    try:
+        alone = {probe.idx: _factors(probe.n, probe.r)}
+        recs, _ = serve.run(sv, [probe], A, B, smp.SMP_BF16, keep=alone)
+        assert len(recs) == 1
+        mixed = {probe.idx: _factors(probe.n, probe.r)}
+        recs, _ = serve.run(sv, jobs, A, B, smp.SMP_BF16, keep=mixed)
+        assert sorted(r["idx"] for r in recs) == list(range(12))
+        assert all(r["latency_ms"] > 0 for r in recs)
+    finally:
+        smp.smp_serve_destroy(sv)
+    for a, b in zip(alone[probe.idx], mixed[probe.idx]):
+        assert torch.equal(a, b)
+    # the same job through the plain pipeline (one context on torch's stream): the same bits again
+    s = pipeline.Solver(probe.n, probe.n, probe.k, torch.bfloat16, seed=2 * probe.seed + 1, max_rows=32768)
+    a = A[probe.row_offset:probe.row_offset + probe.d, :probe.n]
+    b = B[probe.row_offset:probe.row_offset + probe.d, :probe.n]
+    out = s.solve(a, b, probe.r, probe.T, m=probe.m, sample_seed=2 * probe.seed + 2, walt_seed=2 * probe.seed + 3,
+                  block_rows=32768)
+    for got, key in zip(alone[probe.idx], ("U", "S", "V")):
+        assert torch.equal(got, out[key])
+    s.close()
+
+
+def test_admission_by_budget(env):
+    smp, pipeline, A, B = env
+    j = _jobs(1, seed=3)[0]
+    need = smp.smp_serve_job_bytes(j.params(smp.SMP_BF16))
+    sv = smp.smp_serve_create(int(need * 1.5), solve_workers=1)
+    try:
+        first = smp.smp_serve_admit(sv, j.params(smp.SMP_BF16))
+        assert first is not None
+        assert smp.smp_serve_admit(sv, j.params(smp.SMP_BF16)) is None          # SMP_EBUSY
+        used, live = smp.smp_serve_stats(sv)
+        assert used == need and live == 1
+        smp.smp_serve_cancel(sv, first)
+        assert smp.smp_serve_stats(sv) == (0, 0)
+        second = smp.smp_serve_admit(sv, j.params(smp.SMP_BF16))
+        assert second is not None
+        for r0, nr in serve.block_plan(j.d, 32768):
+            a = A[j.row_offset + r0:j.row_offset + r0 + nr, :j.n]
+            b = B[j.row_offset + r0:j.row_offset + r0 + nr, :j.n]
+            smp.smp_serve_block(sv, second, a, A.stride(0), b, B.stride(0), r0, nr)
+        smp.smp_serve_close(sv, second)
+        with pytest.raises(smp.SmpError) as e:                                   # closed: no more blocks
+            smp.smp_serve_block(sv, second, a, A.stride(0), b, B.stride(0), 0, 16)
+        assert e.value.status == smp.SMP_ESTATE
+        nnz, lat = smp.smp_serve_collect(sv, second)
+        assert nnz > 0 and lat > 0
+        assert smp.smp_serve_stats(sv) == (0, 0)
+    finally:
+        smp.smp_serve_destroy(sv)
+
+
+def test_cancel_streaming_and_queued_jobs(env):
+    smp, pipeline, A, B = env
+    jobs = _jobs(3, seed=11)
+    sv = smp.smp_serve_create(8 << 30, solve_workers=1)
+    try:
+        ids = [smp.smp_serve_admit(sv, j.params(smp.SMP_BF16)) for j in jobs]
+        j0 = jobs[0]
+        a = A[j0.row_offset:j0.row_offset + 1024, :j0.n]
+        b = B[j0.row_offset:j0.row_offset + 1024, :j0.n]
+        smp.smp_serve_block(sv, ids[0], a, A.stride(0), b, B.stride(0), 0, 1024)
+        smp.smp_serve_cancel(sv, ids[0])                                         # streaming
+        for jid, j in zip(ids[1:], jobs[1:]):
+            for r0, nr in serve.block_plan(j.d, 32768):
+                smp.smp_serve_block(sv, jid, A[j.row_offset + r0:j.row_offset + r0 + nr, :j.n], A.stride(0),
+                                    B[j.row_offset + r0:j.row_offset + r0 + nr, :j.n], B.stride(0), r0, nr)
+            smp.smp_serve_close(sv, jid)
+        smp.smp_serve_cancel(sv, ids[2])                                         # queued or solving
+        nnz, lat = smp.smp_serve_collect(sv, ids[1])
+        assert nnz > 0
+        with pytest.raises(smp.SmpError):
+            smp.smp_serve_poll(sv, ids[2])                                       # gone
+        assert smp.smp_serve_stats(sv) == (0, 0)
+    finally:
+        smp.smp_serve_destroy(sv)

@@ -1,0 +1,59 @@
+"""Host-side logic of the serving form: the admission charge (libsmp's smp_serve_job_bytes, a host function) and
+the request generator / block interleaving of paper_1610_06656_gb300.serve. No GPU."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1610_06656_gb300 import build, serve
+from paper_1610_06656_gb300 import smp as S
+
+
+@pytest.fixture(scope="module")
+def lib():
+    S.load(build.build())
+    return S
+
+
+def test_job_bytes_grows_with_every_size(lib):
+    base = dict(n1=1000, n2=800, k=80, r=10, T=10, m=50000.0, seed=1, sample_seed=2, walt_seed=3)
+    b0 = lib.smp_serve_job_bytes(lib.job_params(**base))
+    for key, val in (("n1", 2000), ("n2", 1600), ("k", 160), ("r", 20), ("m", 200000.0)):
+        kw = dict(base)
+        kw[key] = val
+        assert lib.smp_serve_job_bytes(lib.job_params(**kw)) > b0, key
+    # the sketch partials alone: 9 x (n1 + n2) x ldk x 4 bytes
+    assert b0 > 9 * 1800 * 80 * 4
+
+
+def test_job_bytes_rejects_bad_params(lib):
+    with pytest.raises(lib.SmpError) as e:
+        lib.smp_serve_job_bytes(lib.job_params(n1=0, n2=10, k=8, r=1, T=1, m=10.0, seed=1, sample_seed=2,
+                                               walt_seed=3))
+    assert e.value.status == lib.SMP_EINVAL
+
+
+def test_poisson_arrivals_and_sizes():
+    jobs = serve.poisson_jobs(4000, 200.0, seed=3, pool_rows=1_000_000)
+    gaps = np.diff([0.0] + [j.arrival for j in jobs])
+    assert abs(gaps.mean() * 200.0 - 1.0) < 0.05                 # mean inter-arrival 1 / rate
+    assert abs(gaps.std() / gaps.mean() - 1.0) < 0.05             # exponential: coefficient of variation 1
+    for j in jobs[:200]:
+        assert 64 <= j.n <= 2048 and j.n % 8 == 0 and 10_000 <= j.d <= 500_000
+        assert j.k == 8 * j.r and j.r in (5, 10, 20)
+        assert j.row_offset + j.d <= 1_000_000
+        assert j.m == pytest.approx(4 * j.n * j.r * math.log(j.n))
+
+
+def test_round_robin_interleaves_and_retires():
+    rr = serve.RoundRobin()
+    rr.add(1, "a", serve.block_plan(70000, 32768))     # 3 blocks, last partial
+    rr.add(2, "b", serve.block_plan(10000, 32768))     # 1 block
+    p1 = rr.next_pass()
+    assert [(j, b, last) for j, _, b, last in p1] == [(1, (0, 32768), False), (2, (0, 10000), True)]
+    rr.add(3, "c", serve.block_plan(32768, 32768))
+    p2 = rr.next_pass()
+    assert [(j, b, last) for j, _, b, last in p2] == [(1, (32768, 32768), False), (3, (0, 32768), True)]
+    p3 = rr.next_pass()
+    assert [(j, b, last) for j, _, b, last in p3] == [(1, (65536, 4464), True)]
+    assert len(rr) == 0
