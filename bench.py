@@ -31,6 +31,10 @@ WORKLOADS = {
     "tiny": dict(d=2000, n1=200, n2=200, L=10, sigma=0.1, alpha=0.5, k=100, r=5, T=10, block=65536),
     # one 65,536-row block of the scale shape (1 GB of inputs): the case the ncu captures of the sketch kernel use
     "block": dict(d=65536, n1=2000, n2=2000, L=20, sigma=0.1, alpha=0.5, k=500, r=10, T=10, block=65536),
+    # serving form: Poisson arrivals, job sizes of the batched config (n in [64, 2048], d in [1e4, 5e5],
+    # r in {5, 10, 20}, k = 8 r), BF16 inputs windowed from a resident pool, 32,768-row blocks, 120 GB budget
+    "serve": dict(rate=200.0, jobs=800, warm_jobs=40, block=32768, pool_rows=1_000_000, width=2048, L=20,
+                  sigma=0.1, alpha=0.5, budget=120e9, workers=6, T=10),
 }
 
 
@@ -187,6 +191,8 @@ def main():
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
+    if args.workload == "serve":
+        return run_serving(args, w)
 
     import torch
     import torch.distributed as dist
@@ -357,6 +363,50 @@ def main():
         dist.barrier()
         dist.destroy_process_group()
     solver.close()
+
+
+def run_serving(args, w):
+    """The serving form (one GPU): Poisson job arrivals at w["rate"] per second through libsmp's server; reports
+    completed solves per second over the run and the latency from each job's last block to its factors."""
+    import torch
+    from paper_1610_06656_gb300 import build, serve, smp, synth
+    smp.load(build.build())
+    torch.cuda.set_device(0)
+    pool_A, pool_B, _, _, _ = synth.lowrank_plus_noise_torch(w["pool_rows"], w["width"], w["width"], w["L"],
+                                                             w["sigma"], w["alpha"], seed=1005, device="cuda",
+                                                             dtype=torch.bfloat16)
+    torch.cuda.synchronize()
+    pool_bytes = 2 * pool_A.numel() * 2
+    server = smp.smp_serve_create(int(w["budget"] - pool_bytes), solve_workers=w["workers"])
+    try:
+        warm = serve.poisson_jobs(w["warm_jobs"], w["rate"], seed=99, pool_rows=w["pool_rows"], T=w["T"])
+        serve.run(server, warm, pool_A, pool_B, smp.SMP_BF16, block_rows=w["block"])
+        jobs = serve.poisson_jobs(w["jobs"], w["rate"], seed=5, pool_rows=w["pool_rows"], T=w["T"])
+        clocks = ClockSampler(0)
+        clocks.start()
+        launches0 = smp.smp_launch_count()
+        records, wall = serve.run(server, jobs, pool_A, pool_B, smp.SMP_BF16, block_rows=w["block"])
+        launches = smp.smp_launch_count() - launches0
+        clk = clocks.stop()
+    finally:
+        smp.smp_serve_destroy(server)
+    lat = sorted(r["latency_ms"] for r in records)
+    streamed = sum(j.d * 2 * j.n * 2 for j in jobs)
+    line = {"metric": "serving: completed solves/s under Poisson arrivals; p50/p99 latency from a job's last "
+                      "block to its factors", "value": len(records) / wall, "unit": "solves/s", "n_gpus": 1,
+            "steps": len(records), "warmup": w["warm_jobs"], "ms_per_step": 1e3 * wall / max(1, len(records)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic (low rank 20 + noise 0.1, column scales (j+1)^-0.5), job inputs are windows of a "
+                    "resident %d x %d BF16 pool pair" % (w["pool_rows"], w["width"]),
+            "config": {"workload": "serve", "arrival_rate_per_s": w["rate"], "jobs": w["jobs"],
+                       "n": "uniform [64, 2048]", "d": "uniform [10000, 500000]", "r": [5, 10, 20], "k": "8 r",
+                       "T": w["T"], "block_rows": w["block"], "budget_bytes": w["budget"],
+                       "pool_bytes_charged": pool_bytes, "solve_workers": w["workers"]},
+            "p50_ms": statistics.median(lat), "p99_ms": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+            "mean_latency_ms": sum(lat) / len(lat), "wall_s": wall, "input_gb_streamed": streamed / 1e9,
+            "input_gbs": streamed / wall / 1e9, "gpu_launches": int(launches), "clocks": clk,
+            "roofline": None, "cpu_baseline": None, "e2e": None}
+    print(json.dumps(line), flush=True)
 
 
 def sketch_traffic(rows_per_launch):
