@@ -17,13 +17,15 @@ from . import smp as S
 class JobSpec:
     """One request: sizes, seeds, arrival time (seconds from the start) and its window of the input pool."""
 
-    def __init__(self, idx, arrival, n, d, r, k, T, m, row_offset, seed):
+    def __init__(self, idx, arrival, n, d, r, k, T, m, row_offset, seed, engine=None):
         self.idx, self.arrival, self.n, self.d, self.r, self.k, self.T = idx, arrival, n, d, r, k, T
-        self.m, self.row_offset, self.seed = m, row_offset, seed
+        self.m, self.row_offset, self.seed, self.engine = m, row_offset, seed, engine
 
     def params(self, dtype, engine=S.SMP_ENGINE_AUTO, block_rows=32768):
+        """Job parameters; the job's own engine (set by an autotuner) wins over the run's."""
+        eng = engine if self.engine is None else self.engine
         return S.job_params(self.n, self.n, self.k, self.r, self.T, self.m, seed=2 * self.seed + 1,
-                            sample_seed=2 * self.seed + 2, walt_seed=2 * self.seed + 3, dtype=dtype, engine=engine,
+                            sample_seed=2 * self.seed + 2, walt_seed=2 * self.seed + 3, dtype=dtype, engine=eng,
                             max_rows=block_rows)
 
 

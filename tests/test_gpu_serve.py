@@ -111,3 +111,29 @@ def test_cancel_streaming_and_queued_jobs(env):
         assert smp.smp_serve_stats(sv) == (0, 0)
     finally:
         smp.smp_serve_destroy(sv)
+
+
+def test_batch_matches_single_instance(env):
+    """Eight uneven instances solved together with autotuned engines: one of them equals, bit for bit, the same
+    instance through the plain pipeline with the engine the tuner chose."""
+    smp, pipeline, A, B = env
+    from paper_1610_06656_gb300 import batch
+    A32, B32 = A.float(), B.float()
+    specs = batch.instances(8, seed=13, pool_rows=300_000, n_range=(64, 512), d_range=(10_000, 150_000))
+    tuner = batch.EngineTuner(batch.probe_timer(A32, B32))
+    probe = specs[3]
+    keep = {probe.idx: _factors(probe.n, probe.r)}
+    sv = smp.smp_serve_create(16 << 30, solve_workers=4)
+    try:
+        recs, wall = batch.run(sv, specs, A32, B32, smp.SMP_F32, tuner, block_rows=65536, keep=keep)
+    finally:
+        smp.smp_serve_destroy(sv)
+    assert sorted(r["idx"] for r in recs) == list(range(8)) and wall > 0
+    s = pipeline.Solver(probe.n, probe.n, probe.k, torch.float32, seed=2 * probe.seed + 1, engine=probe.engine,
+                        max_rows=65536)
+    out = s.solve(A32[probe.row_offset:probe.row_offset + probe.d, :probe.n],
+                  B32[probe.row_offset:probe.row_offset + probe.d, :probe.n], probe.r, probe.T, m=probe.m,
+                  sample_seed=2 * probe.seed + 2, walt_seed=2 * probe.seed + 3, block_rows=65536)
+    for got, key in zip(keep[probe.idx], ("U", "S", "V")):
+        assert torch.equal(got, out[key])
+    s.close()

@@ -57,3 +57,27 @@ def test_round_robin_interleaves_and_retires():
     p3 = rr.next_pass()
     assert [(j, b, last) for j, _, b, last in p3] == [(1, (65536, 4464), True)]
     assert len(rr) == 0
+
+
+def test_batch_instances_and_tuner_cache(tmp_path):
+    from paper_1610_06656_gb300 import batch
+    specs = batch.instances(256, seed=4, pool_rows=1_000_000)
+    assert len(specs) == 256 and all(s.arrival == 0.0 and s.k == 8 * s.r for s in specs)
+    calls = []
+
+    def fake(n, k, dtype, engine):          # the tensor-core engine wins from n = 512 up; SIMT cannot run k = 160
+        calls.append((n, k, engine))
+        if engine == S.SMP_ENGINE_SIMT:
+            return None if k == 160 else 1.0
+        return 0.5 if n >= 512 else 2.0
+
+    path = str(tmp_path / "tune.json")
+    t = batch.EngineTuner(fake, cache_path=path)
+    assert t.choose(100, 40, S.SMP_F32) == S.SMP_ENGINE_SIMT
+    assert t.choose(120, 40, S.SMP_F32) == S.SMP_ENGINE_SIMT            # same bucket (128): cached
+    assert t.choose(1000, 40, S.SMP_F32) == S.SMP_ENGINE_TC
+    assert t.choose(100, 160, S.SMP_F32) == S.SMP_ENGINE_TC             # SIMT unavailable
+    assert t.trials == 6 and len(calls) == 6
+    t2 = batch.EngineTuner(fake, cache_path=path)                       # reloaded from the file: no new trials
+    assert t2.choose(1000, 40, S.SMP_F32) == S.SMP_ENGINE_TC and t2.trials == 0
+    assert batch.n_bucket(64) == 64 and batch.n_bucket(65) == 128 and batch.n_bucket(2048) == 2048
