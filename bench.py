@@ -35,6 +35,10 @@ WORKLOADS = {
     # r in {5, 10, 20}, k = 8 r), BF16 inputs windowed from a resident pool, 32,768-row blocks, 120 GB budget
     "serve": dict(rate=200.0, jobs=800, warm_jobs=40, block=32768, pool_rows=1_000_000, width=2048, L=20,
                   sigma=0.1, alpha=0.5, budget=120e9, workers=6, T=10),
+    # precision form: BF16-stored inputs, sketch in BF16 and in FP8 E4M3 (tensor cores) against the FP32 path
+    # (k = 1,024 exceeds the TF32 engine's 512, so FP32 runs on the CUDA-core engine) on the same stored values
+    "precision": dict(d=4_000_000, n1=4096, n2=4096, L=32, sigma=0.05, alpha=0.7, k=1024, r=20, T=15, block=65536,
+                      steps=2, warm=1),
     # batched form: 256 FP32 instances (n in [64, 2048], d in [1e4, 5e5], r in {5, 10, 20}, k = 8 r) solved
     # together, sketch engine per (k, n bucket) from the autotuner
     "batch": dict(instances=256, warm=16, block=65536, pool_rows=1_000_000, width=2048, L=20, sigma=0.1, alpha=0.5,
@@ -199,6 +203,8 @@ def main():
         return run_serving(args, w)
     if args.workload == "batch":
         return run_batched(args, w)
+    if args.workload == "precision":
+        return run_precision(args, w)
 
     import torch
     import torch.distributed as dist
@@ -414,6 +420,74 @@ def run_serving(args, w):
             "mean_latency_ms": sum(lat) / len(lat), "wall_s": wall, "input_gb_streamed": streamed / 1e9,
             "input_gbs": streamed / wall / 1e9, "gpu_launches": int(launches), "clocks": clk,
             "roofline": None, "cpu_baseline": None, "e2e": None}
+    print(json.dumps(line), flush=True)
+
+
+def run_precision(args, w):
+    """The precision form (one GPU): solves/s and spectral error of SMP-PCA with the sketch in BF16, in FP8 E4M3
+    (tensor cores) and in FP32 (CUDA cores) on the same BF16-stored inputs; WAltMin's solves in binary64."""
+    import torch
+    from paper_1610_06656_gb300 import build, pipeline, smp, synth
+    smp.load(build.build())
+    torch.cuda.set_device(0)
+    A, B, _, _, _ = synth.lowrank_plus_noise_torch(w["d"], w["n1"], w["n2"], w["L"], w["sigma"], w["alpha"],
+                                                  seed=1002, device="cuda", dtype=torch.bfloat16)
+    torch.cuda.synchronize()
+    m = pipeline.default_m(w["n1"], w["n2"], w["r"])
+    stream = torch.cuda.current_stream()
+    results = {}
+    peaks, _ = measured_peaks()
+    forms = (("bf16", torch.bfloat16, smp.SMP_ENGINE_TC), ("fp8_e4m3", torch.bfloat16, smp.SMP_ENGINE_TC_FP8),
+             ("fp32", torch.float32, smp.SMP_ENGINE_SIMT))
+    factors = []
+    for name, tdt, eng in forms:
+        Xa, Xb = (A, B) if tdt == torch.bfloat16 else (A.float(), B.float())
+        solver = pipeline.Solver(w["n1"], w["n2"], w["k"], tdt, seed=1, engine=eng, max_rows=w["block"])
+        sk_ms = []
+
+        def step():
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            solver.sketch(Xa, Xb, w["block"])
+            e1.record(stream)
+            nnz = solver.sample(m, 2)
+            out = solver.waltmin(solver.estimate(nnz), w["r"], w["T"], 0, 3)
+            sk_ms.append(e0.elapsed_time(e1))
+            return out, nnz
+
+        for _ in range(w["warm"]):
+            step()
+        torch.cuda.synchronize()
+        sk_ms.clear()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(w["steps"]):
+            (U, S, V), nnz = step()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / w["steps"]
+        in_bytes = w["d"] * (w["n1"] + w["n2"]) * (2 if tdt == torch.bfloat16 else 4)
+        flops = 2.0 * w["k"] * w["d"] * (w["n1"] + w["n2"])
+        results[name] = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms, "sketch_ms": sum(sk_ms) / len(sk_ms),
+                         "sketch_tflops": flops / (sum(sk_ms) / len(sk_ms)) / 1e9,
+                         "sketch_gbs": in_bytes / (sum(sk_ms) / len(sk_ms)) / 1e6, "nnz": int(nnz)}
+        factors.append((U.clone(), S.clone(), V.clone()))
+        solver.close()
+        del Xa, Xb
+        torch.cuda.empty_cache()
+    errs, opt = spectral_error(torch, A, B, factors)
+    for (name, _, _), e in zip(forms, errs):
+        results[name]["spectral_err"] = e
+    line = {"metric": "precision form: solves/s and spectral error per sketch precision (same BF16-stored inputs)",
+            "value": results["bf16"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": w["steps"],
+            "warmup": w["warm"], "ms_per_step": results["bf16"]["ms_per_solve"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic (low rank 32 + noise 0.05, column scales (j+1)^-0.7), stored in BF16",
+            "config": {"workload": "precision", **{k: w[k] for k in ("d", "n1", "n2", "k", "r", "T")},
+                       "block_rows": w["block"], "m": m, "l2": "inputs (65.5 GB) larger than L2; no flush"},
+            "forms": results, "optimal_err": opt, "bf16_peak_tflops": peaks["bf16_tflops"],
+            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None}
     print(json.dumps(line), flush=True)
 
 

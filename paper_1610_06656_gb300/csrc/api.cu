@@ -2,6 +2,8 @@
 // the kernels of sketch*.cu, sample.cu, estimate.cu and waltmin.cu; this file only validates and dispatches.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -58,9 +60,23 @@ void free_ctx(smp_ctx* c) {
                     c->col,    c->qhat,   c->csc_row, c->csc_pos, c->alpha,   c->beta,  c->mask,    c->wpre,
                     c->erow,   c->srht_y, c->srht_nsq, c->srht_rows, c->mn_S,   c->mn_bcum, c->mn_btot, c->mn_rows, c->mn_off, c->mn_draw, c->mn_count,
                     c->row_cnt, c->col_cnt, c->dev_err};
+    // stream-ordered frees: no device-wide synchronisation, so other contexts' work keeps running
     for (void* p : ptrs)
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, c->stream);
     delete c;
+}
+
+// Context memory comes from the device's default stream-ordered pool; keep what contexts free cached there for the
+// next ones instead of returning it to the driver at every synchronisation (a process-local pool setting).
+void keep_pool_memory(int device) {
+    static std::once_flag once;
+    std::call_once(once, [device] {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+    });
 }
 
 bool elem_size(int dtype, size_t* sz) {
@@ -122,12 +138,13 @@ smp_status smp_sketch_begin(const smp_params* params, void* stream, smp_ctx** ou
         return s;
     }
     c->splits = 8;
+    keep_pool_memory(c->device);
     const size_t acc = (size_t)c->acc_bytes;
     const int64_t n1 = p.n1, n2 = p.n2;
     bool ok = true;
     auto alloc = [&](void** ptr, size_t bytes) {
         if (!ok) return;
-        if (cudaMalloc(ptr, std::max<size_t>(bytes, 16)) != cudaSuccess) ok = false;
+        if (cudaMallocAsync(ptr, std::max<size_t>(bytes, 16), c->stream) != cudaSuccess) ok = false;
     };
     alloc(&c->part, (size_t)c->splits * c->ntot * c->ldk * acc);
     alloc((void**)&c->nsq, (size_t)c->splits * c->ntot * 8);

@@ -313,12 +313,12 @@ __global__ void mn_qhat_kernel(const int32_t* __restrict__ erow, const int32_t* 
 }
 
 template <typename T>
-cudaError_t ensure(T*& p, int64_t& have, int64_t need) {
+cudaError_t ensure(T*& p, int64_t& have, int64_t need, cudaStream_t st) {
     if (have >= need && p) return cudaSuccess;
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, st);
     p = nullptr;
     have = 0;
-    cudaError_t e = cudaMalloc((void**)&p, (size_t)std::max<int64_t>(need, 1) * sizeof(T));
+    cudaError_t e = cudaMallocAsync((void**)&p, (size_t)std::max<int64_t>(need, 1) * sizeof(T), st);
     if (e == cudaSuccess) have = need;
     return e;
 }
@@ -330,13 +330,13 @@ smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out, boo
     const int64_t W = (n2 + 31) / 32;
     cudaStream_t st = c->stream;
     if (c->mask_words < n1 * W) {
-        if (c->mask) cudaFree(c->mask);
-        if (c->wpre) cudaFree(c->wpre);
+        if (c->mask) cudaFreeAsync(c->mask, st);
+        if (c->wpre) cudaFreeAsync(c->wpre, st);
         c->mask = nullptr;
         c->wpre = nullptr;
         c->mask_words = 0;
-        if (cudaMalloc((void**)&c->mask, (size_t)(n1 * W) * 4) != cudaSuccess ||
-            cudaMalloc((void**)&c->wpre, (size_t)(n1 * W) * 4) != cudaSuccess)
+        if (cudaMallocAsync((void**)&c->mask, (size_t)(n1 * W) * 4, st) != cudaSuccess ||
+            cudaMallocAsync((void**)&c->wpre, (size_t)(n1 * W) * 4, st) != cudaSuccess)
             return fail(c, SMP_ENOMEM, "smp_sample: cannot allocate the coin bit words");
         c->mask_words = n1 * W;
     }
@@ -353,11 +353,11 @@ smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out, boo
     } else {
         const int64_t nb = (n2 + MN_BLOCK - 1) / MN_BLOCK;
         if (!c->mn_S) {
-            if (cudaMalloc((void**)&c->mn_S, (size_t)n1 * 8) != cudaSuccess ||
-                cudaMalloc((void**)&c->mn_bcum, (size_t)n2 * 8) != cudaSuccess ||
-                cudaMalloc((void**)&c->mn_btot, (size_t)nb * 8) != cudaSuccess ||
-                cudaMalloc((void**)&c->mn_rows, (size_t)n1 * 4) != cudaSuccess ||
-                cudaMalloc((void**)&c->mn_off, (size_t)(n1 + 1) * 8) != cudaSuccess)
+            if (cudaMallocAsync((void**)&c->mn_S, (size_t)n1 * 8, st) != cudaSuccess ||
+                cudaMallocAsync((void**)&c->mn_bcum, (size_t)n2 * 8, st) != cudaSuccess ||
+                cudaMallocAsync((void**)&c->mn_btot, (size_t)nb * 8, st) != cudaSuccess ||
+                cudaMallocAsync((void**)&c->mn_rows, (size_t)n1 * 4, st) != cudaSuccess ||
+                cudaMallocAsync((void**)&c->mn_off, (size_t)(n1 + 1) * 8, st) != cudaSuccess)
                 return fail(c, SMP_ENOMEM, "smp_sample_multinomial: cannot allocate the row tables");
         }
         if ((e = cudaMemsetAsync(c->mask, 0, (size_t)(n1 * W) * 4, st)) != cudaSuccess)
@@ -373,10 +373,10 @@ smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out, boo
             (e = cudaStreamSynchronize(st)) != cudaSuccess)
             return check_cuda(c, e, "smp_sample_multinomial draw count");
         if (ndraw > c->mn_draw_cap) {
-            if (c->mn_draw) cudaFree(c->mn_draw);
+            if (c->mn_draw) cudaFreeAsync(c->mn_draw, st);
             c->mn_draw = nullptr;
             c->mn_draw_cap = 0;
-            if (cudaMalloc((void**)&c->mn_draw, (size_t)ndraw * 4) != cudaSuccess)
+            if (cudaMallocAsync((void**)&c->mn_draw, (size_t)ndraw * 4, st) != cudaSuccess)
                 return fail(c, SMP_ENOMEM, "smp_sample_multinomial: cannot allocate the draws");
             c->mn_draw_cap = ndraw;
         }
@@ -396,9 +396,9 @@ smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out, boo
     if (nnz > c->cap) {
         int64_t have = c->cap, h2 = c->cap, h3 = c->cap, h4 = c->cap, h5 = c->cap;
         const int64_t want = nnz + nnz / 8 + 1024;
-        if (ensure(c->col, have, want) != cudaSuccess || ensure(c->qhat, h2, want) != cudaSuccess ||
-            ensure(c->csc_row, h3, want) != cudaSuccess || ensure(c->csc_pos, h4, want) != cudaSuccess ||
-            ensure(c->erow, h5, want) != cudaSuccess)
+        if (ensure(c->col, have, want, st) != cudaSuccess || ensure(c->qhat, h2, want, st) != cudaSuccess ||
+            ensure(c->csc_row, h3, want, st) != cudaSuccess || ensure(c->csc_pos, h4, want, st) != cudaSuccess ||
+            ensure(c->erow, h5, want, st) != cudaSuccess)
             return fail(c, SMP_ENOMEM, "smp_sample: cannot allocate Omega");
         c->cap = want;
     }
@@ -409,10 +409,10 @@ smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out, boo
                                                       c->csc_pos);
         if (multinomial) {
             if (nnz > c->mn_count_cap) {
-                if (c->mn_count) cudaFree(c->mn_count);
+                if (c->mn_count) cudaFreeAsync(c->mn_count, st);
                 c->mn_count = nullptr;
                 c->mn_count_cap = 0;
-                if (cudaMalloc((void**)&c->mn_count, (size_t)c->cap * 4) != cudaSuccess)
+                if (cudaMallocAsync((void**)&c->mn_count, (size_t)c->cap * 4, st) != cudaSuccess)
                     return fail(c, SMP_ENOMEM, "smp_sample_multinomial: cannot allocate the counts");
                 c->mn_count_cap = c->cap;
             }

@@ -118,7 +118,7 @@ void release_job(smp_server* sv, int64_t id) {   // caller holds sv->mu; the job
     Job* j = it->second.get();
     if (j->stream) cudaStreamSynchronize(j->stream);
     if (j->ctx) smp_destroy(j->ctx);
-    if (j->U) cudaFree(j->U);
+    if (j->U) cudaFreeAsync(j->U, j->stream);
     if (j->stream) cudaStreamDestroy(j->stream);
     sv->used -= j->bytes;
     sv->jobs.erase(it);
@@ -197,7 +197,8 @@ smp_status smp_serve_admit(smp_server* sv, const smp_job_params* jp, int64_t* jo
         return SMP_ECUDA;
     }
     s = smp_sketch_begin(&jp->sketch, j->stream, &j->ctx);
-    if (s == SMP_OK && cudaMalloc((void**)&j->U, (size_t)(n1 + n2 + 1) * r * 8) != cudaSuccess) s = SMP_ENOMEM;
+    if (s == SMP_OK && cudaMallocAsync((void**)&j->U, (size_t)(n1 + n2 + 1) * r * 8, j->stream) != cudaSuccess)
+        s = SMP_ENOMEM;
     if (s != SMP_OK) {
         if (j->ctx) smp_destroy(j->ctx);
         cudaStreamDestroy(j->stream);

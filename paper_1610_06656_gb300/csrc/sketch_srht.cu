@@ -222,9 +222,9 @@ cudaError_t launch_sketch_srht(smp_ctx* c, const void* A, int64_t lda, const voi
     const int k = c->p.k;
     cudaStream_t st = c->stream;
     if (!c->srht_y) {
-        cudaError_t e = cudaMalloc((void**)&c->srht_y, (size_t)R * SR_GROUP * 4);
-        if (e == cudaSuccess) e = cudaMalloc((void**)&c->srht_nsq, (size_t)(R / SR_CHUNK) * SR_GROUP * 8);
-        if (e == cudaSuccess) e = cudaMalloc((void**)&c->srht_rows, (size_t)(257 + 2 * 1024) * 4);
+        cudaError_t e = cudaMallocAsync((void**)&c->srht_y, (size_t)R * SR_GROUP * 4, st);
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&c->srht_nsq, (size_t)(R / SR_CHUNK) * SR_GROUP * 8, st);
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&c->srht_rows, (size_t)(257 + 2 * 1024) * 4, st);
         if (e != cudaSuccess) return e;
         static std::atomic<bool> attr{false};
         if (!attr) {

@@ -419,14 +419,17 @@ cudaError_t ensure_pi_buffers(smp_ctx* c, size_t bytes) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // no sketch still reads the old buffers
     if (e != cudaSuccess) return e;
     for (int b = 0; b < 2; ++b) {
-        if (c->pi_buf[b]) cudaFree(c->pi_buf[b]);
+        if (c->pi_buf[b]) cudaFreeAsync(c->pi_buf[b], c->stream);
         c->pi_buf[b] = nullptr;
         c->pi_row0[b] = -1;
         c->pi_nrows[b] = 0;
     }
     c->pi_buf_bytes = 0;
     for (int b = 0; b < 2; ++b) {
-        e = cudaMalloc(&c->pi_buf[b], bytes);
+        // stream-ordered on the context's stream; the side stream's first generation into the buffer waits for
+        // pi_free[b], recorded here after the allocation
+        e = cudaMallocAsync(&c->pi_buf[b], bytes, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(c->pi_free[b], c->stream);
         if (e != cudaSuccess) return e;
     }
     c->pi_buf_bytes = bytes;
@@ -547,11 +550,11 @@ cudaError_t tc_speculate_first_block(smp_ctx* c) {
 }
 
 void release_tc(smp_ctx* c) {
-    if (c->gen_stream) cudaStreamSynchronize(c->gen_stream);
-    if (c->fp8_ws) cudaFree(c->fp8_ws);
+    if (c->gen_stream) cudaStreamSynchronize(c->gen_stream);   // the side stream is done with the buffers
+    if (c->fp8_ws) cudaFreeAsync(c->fp8_ws, c->stream);
     c->fp8_ws = nullptr;
     for (int b = 0; b < 2; ++b) {
-        if (c->pi_buf[b]) cudaFree(c->pi_buf[b]);
+        if (c->pi_buf[b]) cudaFreeAsync(c->pi_buf[b], c->stream);
         if (c->pi_ready[b]) cudaEventDestroy(c->pi_ready[b]);
         if (c->pi_free[b]) cudaEventDestroy(c->pi_free[b]);
         c->pi_buf[b] = nullptr;
