@@ -189,7 +189,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="scale", choices=sorted(WORKLOADS))
-    ap.add_argument("--engine", default="auto", choices=["auto", "simt", "tc"])
+    ap.add_argument("--engine", default="auto", choices=["auto", "simt", "tc", "srht"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-error", action="store_true")
@@ -217,7 +217,8 @@ def main():
     smp.load(build.build() if rank == 0 or world == 1 else build.LIB_PATH)
     if world > 1:
         dist.barrier()
-    engine = {"auto": smp.SMP_ENGINE_AUTO, "simt": smp.SMP_ENGINE_SIMT, "tc": smp.SMP_ENGINE_TC}[args.engine]
+    engine = {"auto": smp.SMP_ENGINE_AUTO, "simt": smp.SMP_ENGINE_SIMT, "tc": smp.SMP_ENGINE_TC,
+              "srht": smp.SMP_ENGINE_SRHT}[args.engine]
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     A, B, _, _, _ = synth.lowrank_plus_noise_torch(w["d"], w["n1"], w["n2"], w["L"], w["sigma"], w["alpha"],
@@ -286,7 +287,11 @@ def main():
     sk_flops = 2.0 * w["k"] * sum(sk_rows) * ntot / len(sk_rows)
     sk_avg_s = sum(sk_ms) / len(sk_ms) / 1e3
     tc_used = engine == smp.SMP_ENGINE_TC or (engine == smp.SMP_ENGINE_AUTO and tc_active(smp))
-    if tc_used:
+    srht = engine == smp.SMP_ENGINE_SRHT
+    if srht:
+        roof = {"bound": "hbm", "achieved": sk_bytes / sk_avg_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "peak_kind": "%s HBM copy" % peak_kind}
+    elif tc_used:
         tf32_peak = peaks["bf16_tflops"] * (1.1 / 2.25)
         roof = {"bound": "tensor", "achieved": sk_flops / sk_avg_s / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
                 "peak_kind": "%s bf16 burst x nominal tf32/bf16 ratio 1.1/2.25" % peak_kind}
@@ -297,7 +302,8 @@ def main():
                 "peak_kind": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x %.0f MHz" % clk_mhz}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = sketch_traffic(sum(sk_rows) / len(sk_rows)) if tc_used else None
-    roof["kernel"] = ("smp_sketch_accumulate: sketch_tc_kernel (tcgen05), Pi of the next block generated on a side "
+    roof["kernel"] = ("smp_sketch_accumulate: block SRHT (srht_stage_a/b kernels)" if srht else
+                      "smp_sketch_accumulate: sketch_tc_kernel (tcgen05), Pi of the next block generated on a side "
                       "stream meanwhile" if tc_used else "sketch_simt_kernel")
     roof["hbm_gbs"] = sk_bytes / sk_avg_s / 1e9
     roof["hbm_frac"] = roof["hbm_gbs"] / peaks["hbm_gbs"]
