@@ -302,7 +302,7 @@ def main():
                 "peak_kind": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x %.0f MHz" % clk_mhz}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = sketch_traffic(sum(sk_rows) / len(sk_rows)) if tc_used else None
-    roof["kernel"] = ("smp_sketch_accumulate: block SRHT (srht_stage_a/b kernels)" if srht else
+    roof["kernel"] = ("smp_sketch_accumulate: block SRHT (srht_fused_kernel)" if srht else
                       "smp_sketch_accumulate: sketch_tc_kernel (tcgen05), Pi of the next block generated on a side "
                       "stream meanwhile" if tc_used else "sketch_simt_kernel")
     roof["hbm_gbs"] = sk_bytes / sk_avg_s / 1e9

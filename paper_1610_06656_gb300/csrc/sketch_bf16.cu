@@ -33,9 +33,20 @@ constexpr int MMA_N = 256;           // sketch rows per instruction
 constexpr int KC_CTA = 512;          // sketch rows per CTA (TMEM columns)
 constexpr int MAX_K = 1024;          // two sketch-row halves
 constexpr int BOX_COLS = 64;         // bf16 columns per data box (128 B)
-constexpr int BOX_BYTES = BOX_COLS * 8 * 2;                  // 64 columns x 8 rows
-constexpr int KGROUP_BYTES = (TILE_M / BOX_COLS) * BOX_BYTES;  // one 8-row group of both boxes
-constexpr int DATA_STAGE_BYTES = (KS / 8) * KGROUP_BYTES;    // 128 columns x 32 rows, [8-row group][box]
+#ifndef SMP_BF16_BOX_ROWS
+#define SMP_BF16_BOX_ROWS 32
+#endif
+constexpr int BOX_ROWS = SMP_BF16_BOX_ROWS;   // rows per data box: 8 ([8-row group][box]) or KS ([box][row])
+static_assert(BOX_ROWS == 8 || BOX_ROWS == KS, "data box rows");
+constexpr int BOX_BYTES = BOX_COLS * BOX_ROWS * 2;
+constexpr int KGROUP_BYTES = (TILE_M / BOX_COLS) * BOX_COLS * 8 * 2;   // one 8-row group of both 64-column boxes
+constexpr int DATA_STAGE_BYTES = (KS / 8) * KGROUP_BYTES;              // 128 columns x 32 rows
+// byte offset, within a stage, of 8-row group g of 64-column box b (the MN-major atom the MMA reads)
+__device__ __forceinline__ constexpr int grp_off(int g, int b) {
+    return BOX_ROWS == 8 ? g * KGROUP_BYTES + b * BOX_COLS * 8 * 2 : b * BOX_BYTES + g * BOX_COLS * 8 * 2;
+}
+constexpr uint32_t A_LBO = BOX_ROWS == 8 ? BOX_COLS * 8 * 2 : BOX_BYTES;   // between 64-column atoms
+constexpr uint32_t A_SBO = BOX_ROWS == 8 ? KGROUP_BYTES : BOX_COLS * 8 * 2;   // between 8-row groups
 constexpr int PI_BOX_BYTES = MMA_N * KS * 2;                 // 256 sketch rows x 32 bf16 (64-byte rows)
 constexpr int PI_STAGE_BYTES = (KC_CTA / MMA_N) * PI_BOX_BYTES;
 #ifndef SMP_BF16_DSTAGES
@@ -157,11 +168,11 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_bf16_kernel(const __grid_co
                 const int t = (int)(rs + (int64_t)it * KS);
                 const uint32_t dst = dring + d * DATA_STAGE_BYTES;
 #pragma unroll
-                for (int g = 0; g < KS / 8; ++g)
+                for (int g = 0; g < KS / BOX_ROWS; ++g)
 #pragma unroll
                     for (int b = 0; b < TILE_M / BOX_COLS; ++b)
-                        tma_load_2d(dst + g * KGROUP_BYTES + b * BOX_BYTES, tm_data, (int)col0 + BOX_COLS * b,
-                                    t + 8 * g, dfull_bar(d));
+                        tma_load_2d(dst + grp_off(g * (BOX_ROWS / 8), b), tm_data, (int)col0 + BOX_COLS * b,
+                                    t + BOX_ROWS * g, dfull_bar(d));
             }
             __syncwarp();
         }
@@ -214,7 +225,7 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_bf16_kernel(const __grid_co
                 for (int kk = 0; kk < KS / 16; ++kk) {
                     // A (data) MN-major, 128B swizzle: 64-column atoms 1 KB apart (LBO), 8-row groups 2 KB apart
                     // (SBO), the next 16 rows two groups on; B (Pi) K-major, 64B swizzle, the next 16 rows at +32 B
-                    const uint64_t ad = smem_desc(dbase + kk * 2 * KGROUP_BYTES, BOX_BYTES, KGROUP_BYTES, SWZ_128B);
+                    const uint64_t ad = smem_desc(dbase + grp_off(2 * kk, 0), A_LBO, A_SBO, SWZ_128B);
                     for (int h = 0; h < nh; ++h) {
                         const uint64_t bd = smem_desc(pbase + h * PI_BOX_BYTES + kk * 32, 16, 512, SWZ_64B);
                         mma_bf16(tmem + h * MMA_N, ad, bd, h == nh - 1 ? id_last : id_full,
@@ -246,13 +257,13 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_bf16_kernel(const __grid_co
                 break;
             }
             if (do_norms) {
-                const uint8_t* stage = base_ptr + d * DATA_STAGE_BYTES + box * BOX_BYTES;
+                const uint8_t* stage = base_ptr + d * DATA_STAGE_BYTES;
 #pragma unroll
                 for (int gg = 0; gg < 2; ++gg) {
 #pragma unroll
                     for (int t = 0; t < 8; ++t) {
                         // 128B swizzle: the 16-byte chunk c of box row t sits at chunk c ^ (t & 7)
-                        const uint32_t wv = *(const uint32_t*)(stage + (g0 + gg) * KGROUP_BYTES + t * 128 +
+                        const uint32_t wv = *(const uint32_t*)(stage + grp_off(g0 + gg, box) + t * 128 +
                                                                (((lane >> 2) ^ t) << 4) + ((lane & 3) << 2));
                         two_sum_square_x2(pack2(__uint_as_float(wv << 16), __uint_as_float(wv & 0xFFFF0000u)),
                                           hi2, lo2);
@@ -362,10 +373,11 @@ cudaError_t launch_sketch_bf16(smp_ctx* c, const void* A, int64_t lda, const voi
     const void* Bp = c->p.same_ab ? A : B;
     const int64_t n2 = c->p.same_ab ? 0 : c->p.n2;
     // data boxes: 64 bf16 columns (128 B) x 8 rows, matching the kernel's expect_tx; Pi boxes: 32 x 256
-    if (!make_map(&ma, A, (uint64_t)c->p.n1, (uint64_t)nrows, (uint64_t)lda, BOX_COLS, 8, CU_TENSOR_MAP_SWIZZLE_128B,
+    if (!make_map(&ma, A, (uint64_t)c->p.n1, (uint64_t)nrows, (uint64_t)lda, BOX_COLS, BOX_ROWS,
+                  CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2) ||
         !make_map(&mb, Bp, (uint64_t)(c->p.same_ab ? c->p.n1 : c->p.n2), (uint64_t)nrows,
-                  (uint64_t)(c->p.same_ab ? lda : ldb), BOX_COLS, 8, CU_TENSOR_MAP_SWIZZLE_128B,
+                  (uint64_t)(c->p.same_ab ? lda : ldb), BOX_COLS, BOX_ROWS, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2) ||
         !make_map(&mp, c->pi_buf[buf], (uint64_t)tpad, (uint64_t)gm.kpad, (uint64_t)gm.ld, KS, MMA_N,
                   CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2))

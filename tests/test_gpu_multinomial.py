@@ -77,3 +77,21 @@ def test_state_errors(env):
         s.sample(100.0, 1, sampler="multinomial")
     assert e.value.status == smp.SMP_ESTATE
     s.close()
+
+
+def test_rows_without_draws_and_single_column(env):
+    """Tiny m: most rows round to zero draws (c_i = 0) and contribute no entries; n2 = 1: every draw is column 0."""
+    torch, smp, pipeline = env
+    rng = np.random.default_rng(21)
+    for n1, n2, m in ((300, 40, 50.0), (50, 1, 400.0)):
+        sA = rng.uniform(0.1, 2.0, n1) / (np.arange(n1) + 1.0) ** 2
+        sB = rng.uniform(0.1, 2.0, n2)
+        s = _norms_solver(torch, pipeline, smp, sA, sB)
+        nnz = s.sample(m, 4, sampler="multinomial")
+        rows, cols, qh, cnt = O.sample_omega_multinomial(sA, sB, m, 4)
+        assert nnz == rows.shape[0]
+        om = omega_numpy(s)
+        np.testing.assert_array_equal(csr_rows(om["row_ptr"]), rows)
+        np.testing.assert_array_equal(om["col"], cols)
+        np.testing.assert_array_equal(om["qhat"], qh)
+        s.close()

@@ -137,3 +137,27 @@ def test_batch_matches_single_instance(env):
     for got, key in zip(keep[probe.idx], ("U", "S", "V")):
         assert torch.equal(got, out[key])
     s.close()
+
+
+def test_collect_timeout_and_destroy_with_live_jobs(env):
+    """A zero timeout on a job whose chain cannot have finished returns SMP_ETIMEOUT and keeps the job; destroying
+    the server with streaming, queued and finished jobs releases them all."""
+    smp, pipeline, A, B = env
+    jobs = _jobs(3, seed=17)
+    sv = smp.smp_serve_create(8 << 30, solve_workers=1)
+    try:
+        ids = [smp.smp_serve_admit(sv, j.params(smp.SMP_BF16)) for j in jobs]
+        for jid, j in zip(ids[:2], jobs[:2]):
+            for r0, nr in serve.block_plan(j.d, 32768):
+                smp.smp_serve_block(sv, jid, A[j.row_offset + r0:j.row_offset + r0 + nr, :j.n], A.stride(0),
+                                    B[j.row_offset + r0:j.row_offset + r0 + nr, :j.n], B.stride(0), r0, nr)
+            smp.smp_serve_close(sv, jid)
+        with pytest.raises(smp.SmpError) as e:       # one worker, two chains of milliseconds each: not done yet
+            smp.smp_serve_collect(sv, ids[1], timeout_s=0.0)
+        assert e.value.status == smp.SMP_ETIMEOUT
+        assert smp.smp_serve_stats(sv)[1] == 3
+        with pytest.raises(smp.SmpError) as e:        # streaming job: nothing to collect yet
+            smp.smp_serve_collect(sv, ids[2])
+        assert e.value.status == smp.SMP_ESTATE
+    finally:
+        smp.smp_serve_destroy(sv)
