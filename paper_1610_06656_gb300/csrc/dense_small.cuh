@@ -95,8 +95,21 @@ __global__ void chol_kernel(const double* __restrict__ G, int b, double* R, doub
 // warps: every warp keeps the whole matrix in registers (lane i holds row i), computes each pivot and its column
 // (in parallel, identically), and updates only the trailing columns kk with kk % 4 == its warp id, so the binary64
 // work of the trailing updates is spread over the SM's four sub-partitions (on this part each issues about one
-// binary64 warp instruction per 64 cycles). Column j + 1 is then broadcast from the warp that updated it through
+// binary64 warp instruction per 64 cycles). Each warp runs its own compile-time list of columns (chol32_update<W>):
+// with one shared loop and a runtime warp test the compiler predicates the updates, and the predicated-off binary64
+// instructions still take their issue slots. Column j + 1 is then broadcast from the warp that updated it through
 // shared memory. Launch with 128 threads.
+template <int W>
+__device__ __forceinline__ void chol32_update(double (&a)[32], int j, int b, int lane, double lij) {
+#pragma unroll
+    for (int kk = W; kk < 32; kk += 4) {
+        if (kk <= j) continue;   // resolved at compile time once j is (the caller's loop is unrolled)
+        if (kk >= b) break;
+        const double lkj = __shfl_sync(0xffffffffu, lij, kk);   // L[kk][j]
+        if (lane > j) a[kk] = fma(-lij, lkj, a[kk]);
+    }
+}
+
 __global__ void __launch_bounds__(128) chol32_kernel(const double* __restrict__ G, int b, double* R, double tol) {
     __shared__ double col[2][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -117,12 +130,11 @@ __global__ void __launch_bounds__(128) chol32_kernel(const double* __restrict__ 
             const double y = ok ? rsqrt_refined(d) : 0.0;
             const double lij = lane == j ? (ok ? d * y : 0.0) : (lane > j ? a[j] * y : 0.0);
             if (lane >= j) a[j] = lij;
-#pragma unroll
-            for (int kk = j + 1; kk < 32; ++kk) {
-                if (kk < b && (kk & 3) == w) {
-                    const double lkj = __shfl_sync(0xffffffffu, lij, kk);   // L[kk][j]
-                    if (lane > j) a[kk] = fma(-lij, lkj, a[kk]);
-                }
+            switch (w) {   // warp-uniform
+                case 0: chol32_update<0>(a, j, b, lane, lij); break;
+                case 1: chol32_update<1>(a, j, b, lane, lij); break;
+                case 2: chol32_update<2>(a, j, b, lane, lij); break;
+                default: chol32_update<3>(a, j, b, lane, lij); break;
             }
             if (j + 1 < b) {   // broadcast the next pivot column from the warp that updated it
                 if (((j + 1) & 3) == w) col[(j + 1) & 1][lane] = a[j + 1];
