@@ -193,6 +193,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-error", action="store_true")
+    ap.add_argument("--workers", type=int, default=0, help="solve worker threads of the batched / serving forms")
     ap.add_argument("--no-baseline", action="store_true",
                     help="skip the SVD(A~^T B~) and multinomial-sampling comparisons")
     args = ap.parse_args()
@@ -397,7 +398,8 @@ def run_serving(args, w):
                                                              dtype=torch.bfloat16)
     torch.cuda.synchronize()
     pool_bytes = 2 * pool_A.numel() * 2
-    server = smp.smp_serve_create(int(w["budget"] - pool_bytes), solve_workers=w["workers"])
+    workers = args.workers or w["workers"]
+    server = smp.smp_serve_create(int(w["budget"] - pool_bytes), solve_workers=workers)
     try:
         warm = serve.poisson_jobs(w["warm_jobs"], w["rate"], seed=99, pool_rows=w["pool_rows"], T=w["T"])
         serve.run(server, warm, pool_A, pool_B, smp.SMP_BF16, block_rows=w["block"])
@@ -421,7 +423,7 @@ def run_serving(args, w):
             "config": {"workload": "serve", "arrival_rate_per_s": w["rate"], "jobs": w["jobs"],
                        "n": "uniform [64, 2048]", "d": "uniform [10000, 500000]", "r": [5, 10, 20], "k": "8 r",
                        "T": w["T"], "block_rows": w["block"], "budget_bytes": w["budget"],
-                       "pool_bytes_charged": pool_bytes, "solve_workers": w["workers"]},
+                       "pool_bytes_charged": pool_bytes, "solve_workers": workers},
             "p50_ms": statistics.median(lat), "p99_ms": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
             "mean_latency_ms": sum(lat) / len(lat), "wall_s": wall, "input_gb_streamed": streamed / 1e9,
             "input_gbs": streamed / wall / 1e9, "gpu_launches": int(launches), "clocks": clk,
@@ -517,7 +519,8 @@ def run_batched(args, w):
     for sp in specs:
         tuner.choose(sp.n, sp.k, smp.SMP_F32)
     t_tune = time.perf_counter() - t_tune
-    server = smp.smp_serve_create(int(w["budget"] - pool_bytes), solve_workers=w["workers"])
+    workers = args.workers or w["workers"]
+    server = smp.smp_serve_create(int(w["budget"] - pool_bytes), solve_workers=workers)
     try:
         batch.run(server, batch.instances(w["warm"], seed=98, pool_rows=w["pool_rows"], T=w["T"]), pool_A, pool_B,
                   smp.SMP_F32, tuner, block_rows=w["block"])
@@ -544,7 +547,7 @@ def run_batched(args, w):
                     "resident %d x %d FP32 pool pair" % (w["pool_rows"], w["width"]),
             "config": {"workload": "batch", "instances": w["instances"], "n": "uniform [64, 2048]",
                        "d": "uniform [10000, 500000]", "r": [5, 10, 20], "k": "8 r", "T": w["T"],
-                       "block_rows": w["block"], "solve_workers": w["workers"], "engines": engines,
+                       "block_rows": w["block"], "solve_workers": workers, "engines": engines,
                        "autotune_s": t_tune, "autotune_trials": tuner.trials},
             "wall_s": wall, "input_gb": streamed / 1e9, "input_gbs": streamed / wall / 1e9,
             "hbm_frac": streamed / wall / 1e9 / peaks["hbm_gbs"], "hbm_peak_kind": peak_kind,
