@@ -118,7 +118,11 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_oracle_sample(w, seed_in, rows=16384):
+# rows of the scale workload's single pass the CPU oracle is timed on (about 10 s of host work on the GPU machine)
+CPU_SAMPLE_ROWS = 65536
+
+
+def cpu_oracle_sample(w, seed_in, rows=CPU_SAMPLE_ROWS):
     """Time the CPU oracle on a bounded sample of the workload: the single pass over `rows` of the d rows (scaled
     by d / rows: the pass is linear in d) plus sampling, estimation and WAltMin at full n (independent of d)."""
     import numpy as np
@@ -145,7 +149,7 @@ def run_reference(args, w):
     if rank != 0:
         return
     cores = len(os.sched_getaffinity(0))
-    rows = 16384 if args.workload == "scale" else w["d"]
+    rows = CPU_SAMPLE_ROWS if args.workload == "scale" else w["d"]
     for _ in range(args.warmup):
         cpu_oracle_sample(w, 1001, rows)
     per = []
@@ -356,10 +360,11 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        per, wall = cpu_oracle_sample(w, 1001, 16384 if args.workload == "scale" else w["d"])
+        rows = CPU_SAMPLE_ROWS if args.workload == "scale" else w["d"]
+        per, wall = cpu_oracle_sample(w, 1001, rows)
         cpu = {"value": 1.0 / per, "unit": "solves/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-               "sample": "single pass over 16,384 of 1,000,000 rows (time x d/rows) + sampling, estimate and "
-                         "WAltMin at n = 2,000; %.1f s of CPU wall time" % wall}
+               "sample": "single pass over %d of %d rows (time x d/rows) + sampling, estimate and WAltMin at "
+                         "n = %d; %.1f s of CPU wall time" % (rows, w["d"], w["n1"], wall)}
 
     in_gb = w["d"] * (w["n1"] + w["n2"]) * 4 / 1e9
     l2_note = ("inputs (%.1f GB) larger than L2; no flush" % in_gb) if in_gb > 0.129 else "inputs fit in L2"
