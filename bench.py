@@ -198,6 +198,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-error", action="store_true")
     ap.add_argument("--workers", type=int, default=0, help="solve worker threads of the batched / serving forms")
+    ap.add_argument("--batch-dtype", default="f32", choices=["f32", "bf16"], help="stored inputs of the batched form")
     ap.add_argument("--no-baseline", action="store_true",
                     help="skip the SVD(A~^T B~) and multinomial-sampling comparisons")
     args = ap.parse_args()
@@ -514,42 +515,45 @@ def run_batched(args, w):
     from paper_1610_06656_gb300 import batch, build, smp, synth
     smp.load(build.build())
     torch.cuda.set_device(0)
+    bf16 = args.batch_dtype == "bf16"
+    tdt, sdt, esz = (torch.bfloat16, smp.SMP_BF16, 2) if bf16 else (torch.float32, smp.SMP_F32, 4)
     pool_A, pool_B, _, _, _ = synth.lowrank_plus_noise_torch(w["pool_rows"], w["width"], w["width"], w["L"],
-                                                             w["sigma"], w["alpha"], seed=1004, device="cuda")
+                                                             w["sigma"], w["alpha"], seed=1004, device="cuda",
+                                                             dtype=tdt)
     torch.cuda.synchronize()
-    pool_bytes = 2 * pool_A.numel() * 4
+    pool_bytes = 2 * pool_A.numel() * esz
     tuner = batch.EngineTuner(batch.probe_timer(pool_A, pool_B))
     t_tune = time.perf_counter()
     specs = batch.instances(w["instances"], seed=4, pool_rows=w["pool_rows"], T=w["T"])
     for sp in specs:
-        tuner.choose(sp.n, sp.k, smp.SMP_F32)
+        tuner.choose(sp.n, sp.k, sdt)
     t_tune = time.perf_counter() - t_tune
     workers = args.workers or w["workers"]
     server = smp.smp_serve_create(int(w["budget"] - pool_bytes), solve_workers=workers)
     try:
         batch.run(server, batch.instances(w["warm"], seed=98, pool_rows=w["pool_rows"], T=w["T"]), pool_A, pool_B,
-                  smp.SMP_F32, tuner, block_rows=w["block"])
+                  sdt, tuner, block_rows=w["block"])
         clocks = ClockSampler(0)
         clocks.start()
         launches0 = smp.smp_launch_count()
-        records, wall = batch.run(server, specs, pool_A, pool_B, smp.SMP_F32, tuner, block_rows=w["block"])
+        records, wall = batch.run(server, specs, pool_A, pool_B, sdt, tuner, block_rows=w["block"])
         launches = smp.smp_launch_count() - launches0
         clk = clocks.stop()
     finally:
         smp.smp_serve_destroy(server)
     peaks, peak_kind = measured_peaks()
-    streamed = sum(sp.d * 2 * sp.n * 4 for sp in specs)
+    streamed = sum(sp.d * 2 * sp.n * esz for sp in specs)
     engines = {}
     for sp in specs:
         engines[{smp.SMP_ENGINE_SIMT: "simt", smp.SMP_ENGINE_TC: "tc"}.get(sp.engine, str(sp.engine))] = \
             engines.get({smp.SMP_ENGINE_SIMT: "simt", smp.SMP_ENGINE_TC: "tc"}.get(sp.engine, str(sp.engine)), 0) + 1
     lat = sorted(r["latency_ms"] for r in records)
-    line = {"metric": "batched: instances solved per second (256 uneven FP32 instances together)",
+    line = {"metric": "batched: instances solved per second (256 uneven instances together)",
             "value": len(records) / wall, "unit": "solves/s", "n_gpus": 1, "steps": len(records), "warmup": w["warm"],
             "ms_per_step": 1e3 * wall / max(1, len(records)), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "tf32/f32 per instance (autotuned)",
+            "vs_baseline": None, "dtype": ("bf16" if bf16 else "tf32/f32") + " per instance (autotuned)",
             "data": "synthetic (low rank 20 + noise 0.1, column scales (j+1)^-0.5); instance inputs are windows of a "
-                    "resident %d x %d FP32 pool pair" % (w["pool_rows"], w["width"]),
+                    "resident %d x %d %s pool pair" % (w["pool_rows"], w["width"], "BF16" if bf16 else "FP32"),
             "config": {"workload": "batch", "instances": w["instances"], "n": "uniform [64, 2048]",
                        "d": "uniform [10000, 500000]", "r": [5, 10, 20], "k": "8 r", "T": w["T"],
                        "block_rows": w["block"], "solve_workers": workers, "engines": engines,

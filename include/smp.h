@@ -19,8 +19,8 @@
  *     A kernel that detects a numerical failure records it in a device error word that the next synchronising
  *     call reports (SMP_ENUMERIC / SMP_ETIMEOUT).
  *   - Matrices are row-major. A row block holds data rows [row0, row0 + nrows) of A (nrows x n1, leading
- *     dimension lda elements) and of B (nrows x n2, ldb). Blocks may arrive in any order and any number of
- *     times per row range is an error the library cannot see (it sums what it is given).
+ *     dimension lda elements) and of B (nrows x n2, ldb). Blocks may arrive in any order; a block that overlaps
+ *     rows already accumulated is rejected (smp_sketch_coverage reports what has been seen).
  *   - Randomness: Pi, the sampling coins, the optional Omega split and the start block of the initial subspace
  *     iteration come from Philox4x32-10 (Salmon et al., SC'11) with the counter layouts documented with each
  *     call, so results are a function of (inputs, seeds) only.
@@ -103,8 +103,10 @@ smp_status smp_sketch_begin(const smp_params* params, void* stream, smp_ctx** ou
  * (words 0,1 -> rows 4g, 4g+1; words 2,3 -> rows 4g+2, 4g+3; u1 = ((x>>8)+1) 2^-24, u2 = (x>>8) 2^-24,
  * rho = sqrt(-2 ln u1), z = rho cos(2 pi u2), rho sin(2 pi u2), Pi = z / sqrt(k)).
  * A_blk_dev / B_blk_dev: device, row-major, element type from params.dtype, lda >= n1, ldb >= n2; B ignored when
- * same_ab. 0 <= nrows <= max_rows; nrows = 0 is a no-op. Asynchronous. Errors: SMP_EINVAL, SMP_ESTATE (after
- * finalize), SMP_ECUDA. */
+ * same_ab. 0 <= nrows <= max_rows; nrows = 0 is a no-op. Blocks may arrive in any order; a block overlapping
+ * rows already accumulated since the context was created or reset is rejected (SMP_EINVAL) before anything is
+ * launched, since it would be summed twice. Asynchronous. Errors: SMP_EINVAL, SMP_ESTATE (after finalize),
+ * SMP_ECUDA. */
 smp_status smp_sketch_accumulate(smp_ctx* ctx, const void* A_blk_dev, int64_t lda, const void* B_blk_dev,
                                  int64_t ldb, int64_t row0, int64_t nrows);
 
@@ -310,6 +312,15 @@ smp_status smp_sketch_noalloc(const void* A_dev, int64_t lda, const void* B_dev,
 
 /* Number of CUDA kernels this library has launched since it was loaded (all contexts, all threads). */
 int64_t smp_launch_count(void);
+
+/* Rows accumulated since the context was created or reset: their number, the first row not covered by a
+ * contiguous run from row 0 (0 if row 0 is missing), and the number of disjoint ranges (1 for a complete prefix).
+ * Host only. */
+smp_status smp_sketch_coverage(const smp_ctx* ctx, int64_t* rows, int64_t* first_missing, int64_t* ranges);
+
+/* Fault injection for tests: the next n device allocations made by the library fail (the calls that made them
+ * return SMP_ENOMEM and leave the context usable or destroyable). n <= 0 clears it. Process-wide. */
+void smp_debug_fail_allocs(int32_t n);
 
 #ifdef __cplusplus
 }

@@ -20,6 +20,7 @@ thread_local std::string g_begin_error;
 namespace smp {
 
 std::atomic<uint64_t> g_launches{0};
+std::atomic<int32_t> g_fail_allocs{0};
 
 smp_status fail(smp_ctx* c, smp_status s, const std::string& msg) {
     if (c) c->err = msg;
@@ -88,6 +89,31 @@ bool elem_size(int dtype, size_t* sz) {
     return false;
 }
 
+// Record rows [row0, row0 + nrows) as accumulated; a range that overlaps rows already accumulated since the last
+// reset is rejected (a duplicated row block would be summed twice into the sketch and the norms).
+smp_status track_rows(smp_ctx* c, int64_t row0, int64_t nrows) {
+    const int64_t a = row0, b = row0 + nrows;
+    auto& v = c->seen;
+    auto it = std::upper_bound(v.begin(), v.end(), a,
+                               [](int64_t x, const std::pair<int64_t, int64_t>& r) { return x < r.second; });
+    if (it != v.end() && it->first < b) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "rows [%lld, %lld) overlap rows [%lld, %lld) already accumulated", (long long)a,
+                 (long long)b, (long long)it->first, (long long)it->second);
+        return fail(c, SMP_EINVAL, msg);
+    }
+    it = v.insert(it, {a, b});
+    if (it + 1 != v.end() && (it + 1)->first == b) {   // merge with the range that starts where this one ends
+        it->second = (it + 1)->second;
+        v.erase(it + 1);
+    }
+    if (it != v.begin() && (it - 1)->second == a) {    // and with the one that ends where it starts
+        (it - 1)->second = it->second;
+        v.erase(it);
+    }
+    return SMP_OK;
+}
+
 smp_status check_block(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t nrows) {
     if (!c) return fail(nullptr, SMP_EINVAL, "null context");
     if (c->finalized) return fail(c, SMP_ESTATE, "accumulate after finalize");
@@ -144,7 +170,7 @@ smp_status smp_sketch_begin(const smp_params* params, void* stream, smp_ctx** ou
     bool ok = true;
     auto alloc = [&](void** ptr, size_t bytes) {
         if (!ok) return;
-        if (cudaMallocAsync(ptr, std::max<size_t>(bytes, 16), c->stream) != cudaSuccess) ok = false;
+        if (smp::dev_malloc(ptr, std::max<size_t>(bytes, 16), c->stream) != cudaSuccess) ok = false;
     };
     alloc(&c->part, (size_t)c->splits * c->ntot * c->ldk * acc);
     alloc((void**)&c->nsq, (size_t)c->splits * c->ntot * 8);
@@ -185,11 +211,13 @@ smp_status smp_sketch_accumulate(smp_ctx* c, const void* A, int64_t lda, const v
     if (c->p.engine == SMP_ENGINE_TC_FP8) {
         if (!fp8_block_ok(c, A, lda, B, ldb))
             return fail(c, SMP_EUNSUPPORTED, "the FP8 sketch needs k <= 1024, 16-byte aligned blocks, lda, ldb % 8 == 0");
+        if ((s = track_rows(c, row0, nrows)) != SMP_OK) return s;
         return check_cuda(c, launch_sketch_fp8(c, A, lda, B, ldb, row0, nrows, nullptr, 0), "smp_sketch_accumulate");
     }
     if (c->p.engine == SMP_ENGINE_SRHT) {
         if (!srht_block_ok(c, row0, nrows))
             return fail(c, SMP_EINVAL, "the SRHT sketch takes whole blocks: row0 % max_rows == 0");
+        if ((s = track_rows(c, row0, nrows)) != SMP_OK) return s;
         return check_cuda(c, launch_sketch_srht(c, A, lda, B, ldb, row0, nrows), "smp_sketch_accumulate");
     }
     const bool bf16 = c->p.dtype == SMP_BF16;
@@ -199,6 +227,7 @@ smp_status smp_sketch_accumulate(smp_ctx* c, const void* A, int64_t lda, const v
                     "the tensor-core sketch needs SMP_F32 with k <= 512 and lda, ldb % 4 == 0, or SMP_BF16 with "
                     "k <= 1024 and lda, ldb % 8 == 0, and 16-byte aligned blocks");
     const bool want_tc = c->p.engine == SMP_ENGINE_TC || (c->p.engine == SMP_ENGINE_AUTO && tc_ok);
+    if ((s = track_rows(c, row0, nrows)) != SMP_OK) return s;
     cudaError_t e = !want_tc ? launch_sketch_simt(c, A, lda, B, ldb, row0, nrows, nullptr, 0)
                              : bf16 ? launch_sketch_bf16(c, A, lda, B, ldb, row0, nrows, nullptr, 0)
                                     : launch_sketch_tc(c, A, lda, B, ldb, row0, nrows);
@@ -211,9 +240,11 @@ smp_status smp_sketch_accumulate_pi(smp_ctx* c, const void* Pi, int64_t ldp, con
     if (s != SMP_OK || nrows == 0) return s;
     if (!Pi || ldp < nrows) return fail(c, SMP_EINVAL, "Pi_blk is null or ldp < nrows");
     if (c->p.engine == SMP_ENGINE_SRHT) return fail(c, SMP_EUNSUPPORTED, "the SRHT engine generates its own Pi");
+    if (row0 < 0) return fail(c, SMP_EINVAL, "row0 < 0");
     if (c->p.engine == SMP_ENGINE_TC_FP8) {
         if (!fp8_block_ok(c, A, lda, B, ldb))
             return fail(c, SMP_EUNSUPPORTED, "the FP8 sketch needs k <= 1024, 16-byte aligned blocks, lda, ldb % 8 == 0");
+        if ((s = track_rows(c, row0, nrows)) != SMP_OK) return s;
         return check_cuda(c, launch_sketch_fp8(c, A, lda, B, ldb, row0, nrows, (const float*)Pi, ldp),
                           "smp_sketch_accumulate_pi");
     }
@@ -222,6 +253,7 @@ smp_status smp_sketch_accumulate_pi(smp_ctx* c, const void* Pi, int64_t ldp, con
                             : tc_block_ok(c, A, lda, B, ldb) && ((uintptr_t)Pi % 16 == 0) && (ldp % 4 == 0);
     if (c->p.engine == SMP_ENGINE_TC && !tc_ok)
         return fail(c, SMP_EUNSUPPORTED, "the tensor-core sketch needs 16-byte aligned Pi and ldp % 4 == 0");
+    if ((s = track_rows(c, row0, nrows)) != SMP_OK) return s;
     if (c->p.engine == SMP_ENGINE_TC || (c->p.engine == SMP_ENGINE_AUTO && tc_ok))
         return check_cuda(c,
                           bf16 ? launch_sketch_bf16(c, A, lda, B, ldb, row0, nrows, (const float*)Pi, ldp)
@@ -239,6 +271,7 @@ smp_status smp_sketch_reset(smp_ctx* c) {
     c->finalized = false;
     c->sampled = false;
     c->nnz = 0;
+    c->seen.clear();
     return SMP_OK;
 }
 
@@ -395,5 +428,17 @@ const char* smp_status_string(smp_status s) {
 int32_t smp_version(void) { return 100; }
 
 int64_t smp_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
+void smp_debug_fail_allocs(int32_t n) { g_fail_allocs.store(n > 0 ? n : 0, std::memory_order_relaxed); }
+
+smp_status smp_sketch_coverage(const smp_ctx* c, int64_t* rows, int64_t* first_missing, int64_t* ranges) {
+    if (!c) return fail(nullptr, SMP_EINVAL, "null context");
+    int64_t total = 0;
+    for (const auto& r : c->seen) total += r.second - r.first;
+    if (rows) *rows = total;
+    if (first_missing) *first_missing = (!c->seen.empty() && c->seen.front().first == 0) ? c->seen.front().second : 0;
+    if (ranges) *ranges = (int64_t)c->seen.size();
+    return SMP_OK;
+}
 
 }  // extern "C"

@@ -5,6 +5,8 @@
 #include <atomic>
 #include <cstdint>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/smp.h"
 
@@ -69,6 +71,7 @@ struct smp_ctx {
     void* fp8_ws = nullptr;          // FP8 engine: block maxima, scales, completion counter
     int pi_last = -1;                // buffer the last tensor-core sketch read
     int64_t pi_last_rows = 0;        // largest row block sketched so far
+    std::vector<std::pair<int64_t, int64_t>> seen;   // disjoint sorted [begin, end) row ranges accumulated
     std::string err;
 };
 
@@ -83,6 +86,21 @@ inline G counted(G grid) {
 }
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Device allocations of the library (stream-ordered). smp_debug_fail_allocs(n) makes the next n of them fail with
+// cudaErrorMemoryAllocation: host-side fault injection for the SMP_ENOMEM paths.
+extern std::atomic<int32_t> g_fail_allocs;
+template <typename T>
+inline cudaError_t dev_malloc(T** p, size_t bytes, cudaStream_t st) {
+    int32_t left = g_fail_allocs.load(std::memory_order_relaxed);
+    while (left > 0) {
+        if (g_fail_allocs.compare_exchange_weak(left, left - 1)) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    return cudaMallocAsync((void**)p, bytes, st);
+}
 
 // sketch.cu
 cudaError_t launch_sketch_simt(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t row0,

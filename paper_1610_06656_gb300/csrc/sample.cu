@@ -318,7 +318,7 @@ cudaError_t ensure(T*& p, int64_t& have, int64_t need, cudaStream_t st) {
     if (p) cudaFreeAsync(p, st);
     p = nullptr;
     have = 0;
-    cudaError_t e = cudaMallocAsync((void**)&p, (size_t)std::max<int64_t>(need, 1) * sizeof(T), st);
+    cudaError_t e = dev_malloc((void**)&p, (size_t)std::max<int64_t>(need, 1) * sizeof(T), st);
     if (e == cudaSuccess) have = need;
     return e;
 }
@@ -335,8 +335,8 @@ smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out, boo
         c->mask = nullptr;
         c->wpre = nullptr;
         c->mask_words = 0;
-        if (cudaMallocAsync((void**)&c->mask, (size_t)(n1 * W) * 4, st) != cudaSuccess ||
-            cudaMallocAsync((void**)&c->wpre, (size_t)(n1 * W) * 4, st) != cudaSuccess)
+        if (dev_malloc((void**)&c->mask, (size_t)(n1 * W) * 4, st) != cudaSuccess ||
+            dev_malloc((void**)&c->wpre, (size_t)(n1 * W) * 4, st) != cudaSuccess)
             return fail(c, SMP_ENOMEM, "smp_sample: cannot allocate the coin bit words");
         c->mask_words = n1 * W;
     }
@@ -353,11 +353,11 @@ smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out, boo
     } else {
         const int64_t nb = (n2 + MN_BLOCK - 1) / MN_BLOCK;
         if (!c->mn_S) {
-            if (cudaMallocAsync((void**)&c->mn_S, (size_t)n1 * 8, st) != cudaSuccess ||
-                cudaMallocAsync((void**)&c->mn_bcum, (size_t)n2 * 8, st) != cudaSuccess ||
-                cudaMallocAsync((void**)&c->mn_btot, (size_t)nb * 8, st) != cudaSuccess ||
-                cudaMallocAsync((void**)&c->mn_rows, (size_t)n1 * 4, st) != cudaSuccess ||
-                cudaMallocAsync((void**)&c->mn_off, (size_t)(n1 + 1) * 8, st) != cudaSuccess)
+            if (dev_malloc((void**)&c->mn_S, (size_t)n1 * 8, st) != cudaSuccess ||
+                dev_malloc((void**)&c->mn_bcum, (size_t)n2 * 8, st) != cudaSuccess ||
+                dev_malloc((void**)&c->mn_btot, (size_t)nb * 8, st) != cudaSuccess ||
+                dev_malloc((void**)&c->mn_rows, (size_t)n1 * 4, st) != cudaSuccess ||
+                dev_malloc((void**)&c->mn_off, (size_t)(n1 + 1) * 8, st) != cudaSuccess)
                 return fail(c, SMP_ENOMEM, "smp_sample_multinomial: cannot allocate the row tables");
         }
         if ((e = cudaMemsetAsync(c->mask, 0, (size_t)(n1 * W) * 4, st)) != cudaSuccess)
@@ -376,7 +376,7 @@ smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out, boo
             if (c->mn_draw) cudaFreeAsync(c->mn_draw, st);
             c->mn_draw = nullptr;
             c->mn_draw_cap = 0;
-            if (cudaMallocAsync((void**)&c->mn_draw, (size_t)ndraw * 4, st) != cudaSuccess)
+            if (dev_malloc((void**)&c->mn_draw, (size_t)ndraw * 4, st) != cudaSuccess)
                 return fail(c, SMP_ENOMEM, "smp_sample_multinomial: cannot allocate the draws");
             c->mn_draw_cap = ndraw;
         }
@@ -412,7 +412,7 @@ smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out, boo
                 if (c->mn_count) cudaFreeAsync(c->mn_count, st);
                 c->mn_count = nullptr;
                 c->mn_count_cap = 0;
-                if (cudaMallocAsync((void**)&c->mn_count, (size_t)c->cap * 4, st) != cudaSuccess)
+                if (dev_malloc((void**)&c->mn_count, (size_t)c->cap * 4, st) != cudaSuccess)
                     return fail(c, SMP_ENOMEM, "smp_sample_multinomial: cannot allocate the counts");
                 c->mn_count_cap = c->cap;
             }

@@ -76,7 +76,7 @@ void solve_job(Job* j) {
     if (s == SMP_OK) s = smp_sample(c, j->jp.m, j->jp.sample_seed, &nnz);
     void* vals = nullptr;
     const size_t vbytes = (size_t)std::max<int64_t>(nnz, 1) * (c->acc_bytes == 8 ? 8 : 4);
-    if (s == SMP_OK && cudaMallocAsync(&vals, vbytes, j->stream) != cudaSuccess) s = SMP_ENOMEM;
+    if (s == SMP_OK && smp::dev_malloc(&vals, vbytes, j->stream) != cudaSuccess) s = SMP_ENOMEM;
     if (s == SMP_OK) s = smp_estimate(c, vals);
     if (s == SMP_OK)
         s = smp_waltmin(c, vals, j->jp.r, j->jp.T, j->jp.flags, j->jp.walt_seed, nullptr, j->U, j->S, j->V);
@@ -197,7 +197,7 @@ smp_status smp_serve_admit(smp_server* sv, const smp_job_params* jp, int64_t* jo
         return SMP_ECUDA;
     }
     s = smp_sketch_begin(&jp->sketch, j->stream, &j->ctx);
-    if (s == SMP_OK && cudaMallocAsync((void**)&j->U, (size_t)(n1 + n2 + 1) * r * 8, j->stream) != cudaSuccess)
+    if (s == SMP_OK && smp::dev_malloc((void**)&j->U, (size_t)(n1 + n2 + 1) * r * 8, j->stream) != cudaSuccess)
         s = SMP_ENOMEM;
     if (s != SMP_OK) {
         if (j->ctx) smp_destroy(j->ctx);

@@ -454,7 +454,7 @@ cudaError_t launch_sketch_fp8(smp_ctx* c, const void* A, int64_t lda, const void
     }
     cudaStream_t st = c->stream;
     if (!c->fp8_ws) {   // [0, 8): amax bits of A, B; [8, 16): scales; [16, 20): completion counter
-        cudaError_t e = cudaMallocAsync(&c->fp8_ws, 32, st);
+        cudaError_t e = dev_malloc(&c->fp8_ws, 32, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->fp8_ws, 0, 32, st);
         if (e != cudaSuccess) return e;
     }

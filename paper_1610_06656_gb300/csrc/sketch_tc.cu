@@ -428,7 +428,7 @@ cudaError_t ensure_pi_buffers(smp_ctx* c, size_t bytes) {
     for (int b = 0; b < 2; ++b) {
         // stream-ordered on the context's stream; the side stream's first generation into the buffer waits for
         // pi_free[b], recorded here after the allocation
-        e = cudaMallocAsync(&c->pi_buf[b], bytes, c->stream);
+        e = dev_malloc(&c->pi_buf[b], bytes, c->stream);
         if (e == cudaSuccess) e = cudaEventRecord(c->pi_free[b], c->stream);
         if (e != cudaSuccess) return e;
     }

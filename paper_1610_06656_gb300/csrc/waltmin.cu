@@ -822,7 +822,7 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
     add(nseg_max * (int64_t)b, sizeof(TY));             // SpMM segment partials
     add(nmax * (int64_t)(r * (r + 1) / 2 + r), 8);      // compact per-row systems
     void* ws = nullptr;
-    if (cudaMallocAsync(&ws, need, st) != cudaSuccess) return fail(c, SMP_ENOMEM, "smp_waltmin: scratch");
+    if (dev_malloc(&ws, need, st) != cudaSuccess) return fail(c, SMP_ENOMEM, "smp_waltmin: scratch");
     Arena ar{(char*)ws, 0, need};
     uint8_t* sub = ar.take<uint8_t>(nnz);
     TY* rv = ar.take<TY>(nnz);
@@ -1155,7 +1155,7 @@ smp_status sketch_svd_typed(smp_ctx* c, int r, uint64_t seed, double* U, double*
     add(4 * b * b + 4 * b, 8);                        // G, R1, R2, E, eigenvalues
     add(2 * n1 * r + r * r, 8);                       // Ritz vectors now and at the previous check, their Gram
     void* ws = nullptr;
-    if (cudaMallocAsync(&ws, need, st) != cudaSuccess) return fail(c, SMP_ENOMEM, "smp_sketch_svd: scratch");
+    if (dev_malloc(&ws, need, st) != cudaSuccess) return fail(c, SMP_ENOMEM, "smp_sketch_svd: scratch");
     Arena ar{(char*)ws, 0, need};
     TY* Y = ar.take<TY>(n1 * b);
     TY* Z = ar.take<TY>(n2 * b);

@@ -37,6 +37,8 @@ class smp_job_params(_c.Structure):
 
 # name -> (restype, argtypes), mirroring include/smp.h
 SIGNATURES = {
+    "smp_sketch_coverage": (_i32, [_vp, _c.POINTER(_i64), _c.POINTER(_i64), _c.POINTER(_i64)]),
+    "smp_debug_fail_allocs": (None, [_i32]),
     "smp_serve_job_bytes": (_i32, [_c.POINTER(smp_job_params), _c.POINTER(_i64)]),
     "smp_serve_create": (_i32, [_c.POINTER(smp_server_params), _c.POINTER(_vp)]),
     "smp_serve_admit": (_i32, [_vp, _c.POINTER(smp_job_params), _c.POINTER(_i64)]),
@@ -306,3 +308,15 @@ def smp_serve_stats(server):
 
 def smp_serve_destroy(server):
     _check(load().smp_serve_destroy(server), "smp_serve_destroy")
+
+
+def smp_sketch_coverage(ctx):
+    """(rows accumulated, first row missing from the run that starts at 0, number of disjoint ranges)."""
+    rows, first, ranges = _i64(), _i64(), _i64()
+    _check(load().smp_sketch_coverage(ctx, _c.byref(rows), _c.byref(first), _c.byref(ranges)), "smp_sketch_coverage",
+           ctx)
+    return rows.value, first.value, ranges.value
+
+
+def smp_debug_fail_allocs(n):
+    load().smp_debug_fail_allocs(int(n))
