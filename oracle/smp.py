@@ -454,3 +454,45 @@ def smp_pca(A, B, r, k, m, T, seed, sample_seed, block_rows=65536, same_ab=False
     Uh, Vh = waltmin(st.n1, st.n2, rows, cols, vals, qhat, r, T, st.sA, split, split_seed)
     U, S, V = canonical(Uh, Vh)
     return dict(state=st, rows=rows, cols=cols, qhat=qhat, vals=vals, Uhat=Uh, Vhat=Vh, U=U, S=S, V=V)
+
+
+# --------------------------------------------------------------------------------------------------------------
+# LELA, the two-pass method SMP-PCA is compared with (Section 1; Section 4, Table 1 and Fig. 5(a)): a first pass
+# for the column norms, Omega drawn from the same q_ij (Eq. (1), which SMP-PCA takes over from LELA), a second pass
+# for the exact entries of A^T B on Omega, then the same WAltMin (Algorithm 2).
+# --------------------------------------------------------------------------------------------------------------
+def column_norms_sq(A, B, same_ab=False):
+    """Pass 1: ||A_i||^2 and ||B_j||^2 over all d rows (the norms alone, no sketch)."""
+    A = np.asarray(A, dtype=np.float64)
+    sA = np.einsum("ti,ti->i", A, A)
+    if same_ab:
+        return sA, sA
+    B = np.asarray(B, dtype=np.float64)
+    return sA, np.einsum("tj,tj->j", B, B)
+
+
+def exact_entries(rows, cols, A, B, chunk=1 << 14):
+    """Pass 2: M_ij = A_i^T B_j for every (i, j) of Omega, in the order of rows / cols."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    out = np.empty(len(rows))
+    for s in range(0, len(rows), chunk):
+        r, c = rows[s:s + chunk], cols[s:s + chunk]
+        out[s:s + chunk] = np.einsum("te,te->e", A[:, r], B[:, c])
+    return out
+
+
+def lela(A, B, r, m, T, sample_seed, same_ab=False, split=SPLIT_NONE, split_seed=0, sampler="bernoulli"):
+    """LELA end to end: pass 1 norms, Omega (Bernoulli coins of Eq. (1), or the Appendix's row-wise multinomial
+    draws), pass 2 exact entries, WAltMin on them. Returns the same dict layout as smp_pca (no sketch state)."""
+    A = np.asarray(A, dtype=np.float64)
+    Bm = A if same_ab else np.asarray(B, dtype=np.float64)
+    sA, sB = column_norms_sq(A, Bm, same_ab)
+    if sampler == "multinomial":
+        rows, cols, qhat, _ = sample_omega_multinomial(sA, sB, m, sample_seed)
+    else:
+        rows, cols, qhat = sample_omega(sA, sB, m, sample_seed)
+    vals = exact_entries(rows, cols, A, Bm)
+    Uh, Vh = waltmin(A.shape[1], Bm.shape[1], rows, cols, vals, qhat, r, T, sA, split, split_seed)
+    U, S, V = canonical(Uh, Vh)
+    return dict(sA=sA, sB=sB, rows=rows, cols=cols, qhat=qhat, vals=vals, Uhat=Uh, Vhat=Vh, U=U, S=S, V=V)
