@@ -9,6 +9,12 @@
  *   smp_waltmin                                                      step 5: Algorithm 2 (Appendix A)
  *   smp_sketch_svd                     the baseline SVD(At^T Bt) of Section 4, from the same finalized sketches
  *
+ * LELA, the two-pass method of Section 4 (Table 1) that SMP-PCA is compared with, on the same context:
+ *   smp_norms_accumulate + smp_sketch_finalize   pass 1: ||A_i||, ||B_j|| alone (no sketch)
+ *   smp_sample                                   Omega by Eq. (1), the sampling SMP-PCA takes over from LELA
+ *   smp_exact_accumulate / smp_exact_values      pass 2: the exact entries A_i^T B_j of A^T B over Omega
+ *   smp_waltmin                                  Algorithm 2 on the exact entries
+ *
  * Conventions shared by every call:
  *   - Pointers named *_dev are CUDA device pointers owned by the caller unless stated otherwise. Pointers
  *     returned by the *_view calls are borrowed from the context and stay valid until smp_destroy (or until the
@@ -317,6 +323,40 @@ int64_t smp_launch_count(void);
  * contiguous run from row 0 (0 if row 0 is missing), and the number of disjoint ranges (1 for a complete prefix).
  * Host only. */
 smp_status smp_sketch_coverage(const smp_ctx* ctx, int64_t* rows, int64_t* first_missing, int64_t* ranges);
+
+/* ---------------------------------------------------------------------------------------------------------------
+ * LELA (Section 4, Table 1: the two-pass comparison method). */
+
+/* Pass 1: fold the row block's column sums of squares into the norm accumulators, without a sketch (the
+ * compensated binary32 sums of the sketch engines for SMP_F32 and SMP_BF16 blocks, binary64 for SMP_F64, reduced
+ * over row splits in a fixed order by smp_sketch_finalize). Same block conventions, checks and row tracking as
+ * smp_sketch_accumulate. One pass holds either sketch rows or norms-only rows: mixing them is SMP_ESTATE, and after a
+ * norms-only pass smp_estimate and smp_sketch_svd return SMP_ESTATE. Asynchronous. Errors: SMP_EINVAL, SMP_ESTATE,
+ * SMP_ECUDA. */
+smp_status smp_norms_accumulate(smp_ctx* ctx, const void* A_blk_dev, int64_t lda, const void* B_blk_dev,
+                                int64_t ldb, int64_t row0, int64_t nrows);
+
+/* Pass 2: add sum_{t in block} A[t][i] B[t][j] into the exact entry M_ij = A_i^T B_j of every (i, j) in the
+ * context's Omega (after smp_sample; drawing a new Omega starts the pass afresh). The blocks must cover the same
+ * rows as pass 1 (smp_exact_coverage reports them); a block overlapping rows already added is SMP_EINVAL.
+ * SMP_F32 blocks that are 16-byte aligned with lda, ldb % 4 == 0 run on tensor cores (SMP_ENGINE_AUTO or _TC):
+ * the block of A is transposed into a context buffer of n1 x max_rows floats (allocated on first use), both operands
+ * are rounded to TF32 (round to nearest, ties away), products accumulate in binary32 over a row split of the block
+ * and in binary64 across splits and blocks; |error| <= (2^-10 + rows * 2^-23) sum_t |A[t][i] B[t][j]| with rows
+ * the block's row count. Other blocks (SMP_F64, SMP_BF16, unaligned, SMP_ENGINE_SIMT) run on the CUDA cores in the
+ * context's precision (binary64 for SMP_F64, binary32 otherwise). SMP_ENGINE_TC with a block the tensor-core path
+ * cannot take is SMP_EUNSUPPORTED. Asynchronous. Errors: SMP_ESTATE (before sampling), SMP_EINVAL,
+ * SMP_EUNSUPPORTED, SMP_ENOMEM, SMP_ECUDA. */
+smp_status smp_exact_accumulate(smp_ctx* ctx, const void* A_blk_dev, int64_t lda, const void* B_blk_dev,
+                                int64_t ldb, int64_t row0, int64_t nrows);
+
+/* The exact entries in CSR order (the order of smp_estimate's output, ready for smp_waltmin): the row splits
+ * summed in a fixed order. vals_dev: caller device buffer of nnz floats (doubles for SMP_F64). Asynchronous.
+ * Errors: SMP_ESTATE (no Omega, or no smp_exact_accumulate since it was drawn), SMP_EINVAL. */
+smp_status smp_exact_values(smp_ctx* ctx, void* vals_dev);
+
+/* Rows added by smp_exact_accumulate since Omega was drawn, as smp_sketch_coverage. Host only. */
+smp_status smp_exact_coverage(const smp_ctx* ctx, int64_t* rows, int64_t* first_missing, int64_t* ranges);
 
 /* Fault injection for tests: the next n device allocations made by the library fail (the calls that made them
  * return SMP_ENOMEM and leave the context usable or destroyable). n <= 0 clears it. Process-wide. */

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsmp.so")
-SOURCES = ["api.cu", "sketch.cu", "sketch_tc.cu", "sketch_bf16.cu", "sketch_fp8.cu", "sketch_srht.cu", "sample.cu", "estimate.cu", "waltmin.cu", "noalloc.cu", "serve.cu"]
+SOURCES = ["api.cu", "sketch.cu", "sketch_tc.cu", "sketch_bf16.cu", "sketch_fp8.cu", "sketch_srht.cu", "sample.cu", "estimate.cu", "exact.cu", "waltmin.cu", "noalloc.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
          "--expt-relaxed-constexpr"]

@@ -60,7 +60,7 @@ void free_ctx(smp_ctx* c) {
     void* ptrs[] = {c->part,   c->nsq,    c->sk,      c->s_all,   c->D_all,   c->F,     c->row_ptr, c->col_ptr,
                     c->col,    c->qhat,   c->csc_row, c->csc_pos, c->alpha,   c->beta,  c->mask,    c->wpre,
                     c->erow,   c->srht_y, c->srht_nsq, c->srht_rows, c->mn_S,   c->mn_bcum, c->mn_btot, c->mn_rows, c->mn_off, c->mn_draw, c->mn_count,
-                    c->row_cnt, c->col_cnt, c->dev_err};
+                    c->row_cnt, c->col_cnt, c->ex_part, c->ex_at, c->dev_err};
     // stream-ordered frees: no device-wide synchronisation, so other contexts' work keeps running
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, c->stream);
@@ -89,11 +89,10 @@ bool elem_size(int dtype, size_t* sz) {
     return false;
 }
 
-// Record rows [row0, row0 + nrows) as accumulated; a range that overlaps rows already accumulated since the last
-// reset is rejected (a duplicated row block would be summed twice into the sketch and the norms).
-smp_status track_rows(smp_ctx* c, int64_t row0, int64_t nrows) {
+// Record rows [row0, row0 + nrows) as accumulated in v; a range that overlaps rows already there is rejected (a
+// duplicated row block would be summed twice).
+smp_status track_rows_in(smp_ctx* c, std::vector<std::pair<int64_t, int64_t>>& v, int64_t row0, int64_t nrows) {
     const int64_t a = row0, b = row0 + nrows;
-    auto& v = c->seen;
     auto it = std::upper_bound(v.begin(), v.end(), a,
                                [](int64_t x, const std::pair<int64_t, int64_t>& r) { return x < r.second; });
     if (it != v.end() && it->first < b) {
@@ -111,6 +110,34 @@ smp_status track_rows(smp_ctx* c, int64_t row0, int64_t nrows) {
         (it - 1)->second = it->second;
         v.erase(it);
     }
+    return SMP_OK;
+}
+
+// Rows of the single pass (sketch or norms), since the last reset.
+smp_status track_rows(smp_ctx* c, int64_t row0, int64_t nrows) { return track_rows_in(c, c->seen, row0, nrows); }
+
+// A single pass accumulates either the sketch (with the norms) or the norms alone (LELA's first pass), not both.
+smp_status claim_pass(smp_ctx* c, int kind) {
+    if (c->pass_kind != 0 && c->pass_kind != kind)
+        return fail(c, SMP_ESTATE, kind == 1 ? "sketch rows after norms-only rows in the same pass"
+                                             : "norms-only rows after sketch rows in the same pass");
+    c->pass_kind = kind;
+    return SMP_OK;
+}
+
+// A new Omega invalidates the exact entries accumulated for the previous one.
+void omega_changed(smp_ctx* c) {
+    c->ex_ready = false;
+    c->seen_exact.clear();
+}
+
+smp_status coverage_of(const std::vector<std::pair<int64_t, int64_t>>& v, int64_t* rows, int64_t* first_missing,
+                       int64_t* ranges) {
+    int64_t total = 0;
+    for (const auto& r : v) total += r.second - r.first;
+    if (rows) *rows = total;
+    if (first_missing) *first_missing = (!v.empty() && v.front().first == 0) ? v.front().second : 0;
+    if (ranges) *ranges = (int64_t)v.size();
     return SMP_OK;
 }
 
@@ -208,6 +235,7 @@ smp_status smp_sketch_accumulate(smp_ctx* c, const void* A, int64_t lda, const v
     smp_status s = check_block(c, A, lda, B, ldb, nrows);
     if (s != SMP_OK || nrows == 0) return s;
     if (row0 < 0) return fail(c, SMP_EINVAL, "row0 < 0");
+    if ((s = claim_pass(c, 1)) != SMP_OK) return s;
     if (c->p.engine == SMP_ENGINE_TC_FP8) {
         if (!fp8_block_ok(c, A, lda, B, ldb))
             return fail(c, SMP_EUNSUPPORTED, "the FP8 sketch needs k <= 1024, 16-byte aligned blocks, lda, ldb % 8 == 0");
@@ -241,6 +269,7 @@ smp_status smp_sketch_accumulate_pi(smp_ctx* c, const void* Pi, int64_t ldp, con
     if (!Pi || ldp < nrows) return fail(c, SMP_EINVAL, "Pi_blk is null or ldp < nrows");
     if (c->p.engine == SMP_ENGINE_SRHT) return fail(c, SMP_EUNSUPPORTED, "the SRHT engine generates its own Pi");
     if (row0 < 0) return fail(c, SMP_EINVAL, "row0 < 0");
+    if ((s = claim_pass(c, 1)) != SMP_OK) return s;
     if (c->p.engine == SMP_ENGINE_TC_FP8) {
         if (!fp8_block_ok(c, A, lda, B, ldb))
             return fail(c, SMP_EUNSUPPORTED, "the FP8 sketch needs k <= 1024, 16-byte aligned blocks, lda, ldb % 8 == 0");
@@ -272,6 +301,8 @@ smp_status smp_sketch_reset(smp_ctx* c) {
     c->sampled = false;
     c->nnz = 0;
     c->seen.clear();
+    c->pass_kind = 0;
+    omega_changed(c);
     return SMP_OK;
 }
 
@@ -305,7 +336,10 @@ smp_status smp_sketch_import(smp_ctx* c, const void* At, const void* Bt, const d
     if (!c) return fail(nullptr, SMP_EINVAL, "null context");
     if (!At || !sA || (!c->p.same_ab && (!Bt || !sB))) return fail(c, SMP_EINVAL, "null sketch or norms");
     smp_status s = check_cuda(c, launch_import(c, At, Bt, sA, sB), "smp_sketch_import");
-    if (s == SMP_OK) c->finalized = true;
+    if (s == SMP_OK) {
+        c->finalized = true;
+        c->pass_kind = 1;
+    }
     return s;
 }
 
@@ -318,6 +352,7 @@ smp_status smp_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return check_cuda(c, e, "smp_sample");
     if (!(F[0] > 0.0) && !(F[1] > 0.0)) return fail(c, SMP_EINVAL, "both Frobenius norms are zero");
+    omega_changed(c);
     return run_sample(c, m, seed, nnz_out);
 }
 
@@ -330,6 +365,7 @@ smp_status smp_sample_multinomial(smp_ctx* c, double m, uint64_t seed, int64_t* 
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return check_cuda(c, e, "smp_sample_multinomial");
     if (!(F[0] > 0.0) && !(F[1] > 0.0)) return fail(c, SMP_EINVAL, "both Frobenius norms are zero");
+    omega_changed(c);
     return run_sample(c, m, seed, nnz_out, true);
 }
 
@@ -347,6 +383,7 @@ smp_status smp_sample_from_norms(smp_ctx* c, const double* sA, const double* sB,
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return check_cuda(c, e, "smp_sample_from_norms");
     if (!(F[0] > 0.0) && !(F[1] > 0.0)) return fail(c, SMP_EINVAL, "both Frobenius norms are zero");
+    omega_changed(c);
     return run_sample(c, m, seed, nnz_out);
 }
 
@@ -369,6 +406,7 @@ smp_status smp_estimate(smp_ctx* c, void* vals) {
     if (!c) return fail(nullptr, SMP_EINVAL, "null context");
     if (!c->sampled || !c->finalized) return fail(c, SMP_ESTATE, "smp_estimate needs a finalized sketch and Omega");
     if (!vals && c->nnz > 0) return fail(c, SMP_EINVAL, "null vals");
+    if (c->pass_kind == 2) return fail(c, SMP_ESTATE, "smp_estimate: the pass accumulated norms only (no sketch)");
     return check_cuda(c, launch_estimate(c, vals), "smp_estimate");
 }
 
@@ -391,7 +429,52 @@ smp_status smp_sketch_svd(smp_ctx* c, int32_t r, uint64_t seed, double* U, doubl
     if (r < 1 || r > 32 || r > c->p.n1 || r > c->p.n2 || r > c->p.k)
         return fail(c, SMP_EINVAL, "r out of [1, min(32, n1, n2, k)]");
     if (!U || !S || !V) return fail(c, SMP_EINVAL, "null output");
+    if (c->pass_kind == 2) return fail(c, SMP_ESTATE, "smp_sketch_svd: the pass accumulated norms only (no sketch)");
     return run_sketch_svd(c, r, seed, U, S, V);
+}
+
+smp_status smp_norms_accumulate(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t row0,
+                                int64_t nrows) {
+    smp_status s = check_block(c, A, lda, B, ldb, nrows);
+    if (s != SMP_OK || nrows == 0) return s;
+    if (row0 < 0) return fail(c, SMP_EINVAL, "row0 < 0");
+    if ((s = claim_pass(c, 2)) != SMP_OK) return s;
+    if ((s = track_rows(c, row0, nrows)) != SMP_OK) return s;
+    return check_cuda(c, launch_norms(c, A, lda, B, ldb, nrows), "smp_norms_accumulate");
+}
+
+smp_status smp_exact_accumulate(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t row0,
+                                int64_t nrows) {
+    if (!c) return fail(nullptr, SMP_EINVAL, "null context");
+    if (!c->sampled) return fail(c, SMP_ESTATE, "smp_exact_accumulate before smp_sample");
+    if (nrows < 0 || nrows > c->max_rows) return fail(c, SMP_EINVAL, "nrows out of [0, max_rows]");
+    if (nrows == 0) return SMP_OK;
+    if (row0 < 0) return fail(c, SMP_EINVAL, "row0 < 0");
+    if (!A || lda < c->p.n1) return fail(c, SMP_EINVAL, "A_blk is null or lda < n1");
+    if (!c->p.same_ab && (!B || ldb < c->p.n2)) return fail(c, SMP_EINVAL, "B_blk is null or ldb < n2");
+    const bool tc_ok = exact_tc_ok(c, A, lda, B, ldb);
+    if (c->p.engine == SMP_ENGINE_TC && !tc_ok)
+        return fail(c, SMP_EUNSUPPORTED,
+                    "the tensor-core exact pass needs SMP_F32 and 16-byte aligned blocks with lda, ldb % 4 == 0");
+    const bool use_tc = tc_ok && c->p.engine != SMP_ENGINE_SIMT;
+    if ((use_tc ? (c->p.n1 + 511) / 512 : (c->p.n1 + 31) / 32) > 65535)
+        return fail(c, SMP_EUNSUPPORTED, "smp_exact_accumulate: n1 too large for one launch grid");
+    smp_status s = track_rows_in(c, c->seen_exact, row0, nrows);
+    if (s != SMP_OK) return s;
+    return check_cuda(c, launch_exact(c, A, lda, B, ldb, nrows, use_tc), "smp_exact_accumulate");
+}
+
+smp_status smp_exact_values(smp_ctx* c, void* vals) {
+    if (!c) return fail(nullptr, SMP_EINVAL, "null context");
+    if (!c->sampled) return fail(c, SMP_ESTATE, "smp_exact_values before smp_sample");
+    if (c->seen_exact.empty()) return fail(c, SMP_ESTATE, "smp_exact_values before smp_exact_accumulate");
+    if (!vals && c->nnz > 0) return fail(c, SMP_EINVAL, "null vals");
+    return check_cuda(c, launch_exact_values(c, vals), "smp_exact_values");
+}
+
+smp_status smp_exact_coverage(const smp_ctx* c, int64_t* rows, int64_t* first_missing, int64_t* ranges) {
+    if (!c) return fail(nullptr, SMP_EINVAL, "null context");
+    return coverage_of(c->seen_exact, rows, first_missing, ranges);
 }
 
 smp_status smp_sync(smp_ctx* c) {
@@ -433,12 +516,7 @@ void smp_debug_fail_allocs(int32_t n) { g_fail_allocs.store(n > 0 ? n : 0, std::
 
 smp_status smp_sketch_coverage(const smp_ctx* c, int64_t* rows, int64_t* first_missing, int64_t* ranges) {
     if (!c) return fail(nullptr, SMP_EINVAL, "null context");
-    int64_t total = 0;
-    for (const auto& r : c->seen) total += r.second - r.first;
-    if (rows) *rows = total;
-    if (first_missing) *first_missing = (!c->seen.empty() && c->seen.front().first == 0) ? c->seen.front().second : 0;
-    if (ranges) *ranges = (int64_t)c->seen.size();
-    return SMP_OK;
+    return coverage_of(c->seen, rows, first_missing, ranges);
 }
 
 }  // extern "C"

@@ -72,6 +72,14 @@ struct smp_ctx {
     int pi_last = -1;                // buffer the last tensor-core sketch read
     int64_t pi_last_rows = 0;        // largest row block sketched so far
     std::vector<std::pair<int64_t, int64_t>> seen;   // disjoint sorted [begin, end) row ranges accumulated
+    int pass_kind = 0;               // rows accumulated since the last reset: 0 none, 1 sketch, 2 norms only
+    // LELA's second pass (allocated on first use): exact entries of A^T B over Omega
+    double* ex_part = nullptr;       // [EXACT_SPLITS][ex_cap] row-split partials, CSC order
+    int64_t ex_cap = 0;
+    bool ex_ready = false;           // ex_part cleared for the current Omega
+    float* ex_at = nullptr;          // [n1][max_rows rounded up to 4] TF32 A^T of the current row block
+    size_t ex_at_bytes = 0;
+    std::vector<std::pair<int64_t, int64_t>> seen_exact;   // row ranges of the second pass since Omega was drawn
     std::string err;
 };
 
@@ -161,6 +169,14 @@ smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out, boo
 
 // estimate.cu
 cudaError_t launch_estimate(smp_ctx* c, void* vals);
+
+// exact.cu (LELA's two passes)
+constexpr int EXACT_SPLITS = 4;   // row splits of the exact-entry partials
+cudaError_t launch_norms(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t nrows);
+bool exact_tc_ok(const smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb);
+cudaError_t launch_exact(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t nrows,
+                         bool tensor_cores);
+cudaError_t launch_exact_values(smp_ctx* c, void* vals);
 
 // waltmin.cu
 smp_status run_sketch_svd(smp_ctx* c, int r, uint64_t seed, double* U, double* S, double* V);

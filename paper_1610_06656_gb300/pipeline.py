@@ -84,6 +84,36 @@ class Solver:
         U, Sv, V = self.waltmin(vals, r, T, flags, walt_seed)
         return dict(U=U, S=Sv, V=V, nnz=nnz, vals=vals)
 
+    def norms(self, A, B=None, block_rows=65536, reset=True):
+        """LELA's first pass: stream A, B through smp_norms_accumulate (column norms only), then finalize."""
+        if reset:
+            S.smp_sketch_reset(self.ctx)
+        for r0 in range(0, A.shape[0], block_rows):
+            r1 = min(A.shape[0], r0 + block_rows)
+            b = None if self.same_ab else B[r0:r1]
+            S.smp_norms_accumulate(self.ctx, A[r0:r1], A.stride(0), b, 0 if b is None else B.stride(0), r0, r1 - r0)
+        S.smp_sketch_finalize(self.ctx)
+
+    def exact(self, A, B=None, block_rows=65536):
+        """LELA's second pass over the drawn Omega: the exact entries A_i^T B_j in CSR order."""
+        for r0 in range(0, A.shape[0], block_rows):
+            r1 = min(A.shape[0], r0 + block_rows)
+            b = None if self.same_ab else B[r0:r1]
+            S.smp_exact_accumulate(self.ctx, A[r0:r1], A.stride(0), b, 0 if b is None else B.stride(0), r0, r1 - r0)
+        nnz = S.smp_omega_view(self.ctx)["nnz"]
+        vals = torch.empty(max(nnz, 1), dtype=self.val_dtype, device="cuda")
+        S.smp_exact_values(self.ctx, vals)
+        return vals[:nnz]
+
+    def lela(self, A, B, r, T, m=None, sample_seed=2, walt_seed=3, flags=0, block_rows=65536, sampler="bernoulli"):
+        """LELA end to end (Section 4): norms pass, Omega, exact-entry pass, WAltMin."""
+        m = default_m(self.n1, self.n2, r) if m is None else m
+        self.norms(A, B, block_rows)
+        nnz = self.sample(m, sample_seed, sampler)
+        vals = self.exact(A, B, block_rows)
+        U, Sv, V = self.waltmin(vals, r, T, flags, walt_seed)
+        return dict(U=U, S=Sv, V=V, nnz=nnz, vals=vals)
+
     def omega(self):
         """Omega as torch tensors copied from the context's device arrays (CSR and CSC)."""
         v = S.smp_omega_view(self.ctx)

@@ -38,6 +38,10 @@ class smp_job_params(_c.Structure):
 # name -> (restype, argtypes), mirroring include/smp.h
 SIGNATURES = {
     "smp_sketch_coverage": (_i32, [_vp, _c.POINTER(_i64), _c.POINTER(_i64), _c.POINTER(_i64)]),
+    "smp_norms_accumulate": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _i64]),
+    "smp_exact_accumulate": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _i64]),
+    "smp_exact_values": (_i32, [_vp, _vp]),
+    "smp_exact_coverage": (_i32, [_vp, _c.POINTER(_i64), _c.POINTER(_i64), _c.POINTER(_i64)]),
     "smp_debug_fail_allocs": (None, [_i32]),
     "smp_serve_job_bytes": (_i32, [_c.POINTER(smp_job_params), _c.POINTER(_i64)]),
     "smp_serve_create": (_i32, [_c.POINTER(smp_server_params), _c.POINTER(_vp)]),
@@ -314,6 +318,28 @@ def smp_sketch_coverage(ctx):
     """(rows accumulated, first row missing from the run that starts at 0, number of disjoint ranges)."""
     rows, first, ranges = _i64(), _i64(), _i64()
     _check(load().smp_sketch_coverage(ctx, _c.byref(rows), _c.byref(first), _c.byref(ranges)), "smp_sketch_coverage",
+           ctx)
+    return rows.value, first.value, ranges.value
+
+
+def smp_norms_accumulate(ctx, A_blk, lda, B_blk, ldb, row0, nrows):
+    _check(load().smp_norms_accumulate(ctx, _ptr(A_blk), lda, _ptr(B_blk), ldb, row0, nrows),
+           "smp_norms_accumulate", ctx)
+
+
+def smp_exact_accumulate(ctx, A_blk, lda, B_blk, ldb, row0, nrows):
+    _check(load().smp_exact_accumulate(ctx, _ptr(A_blk), lda, _ptr(B_blk), ldb, row0, nrows),
+           "smp_exact_accumulate", ctx)
+
+
+def smp_exact_values(ctx, vals):
+    _check(load().smp_exact_values(ctx, _ptr(vals)), "smp_exact_values", ctx)
+
+
+def smp_exact_coverage(ctx):
+    """(rows of the exact pass, first row missing from the run that starts at 0, number of disjoint ranges)."""
+    rows, first, ranges = _i64(), _i64(), _i64()
+    _check(load().smp_exact_coverage(ctx, _c.byref(rows), _c.byref(first), _c.byref(ranges)), "smp_exact_coverage",
            ctx)
     return rows.value, first.value, ranges.value
 
