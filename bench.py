@@ -42,6 +42,10 @@ WORKLOADS = {
     # one 65,536-row block of the precision shape (1 GB of BF16 inputs): the case the ncu captures use
     "precision_block": dict(d=65536, n1=4096, n2=4096, L=32, sigma=0.05, alpha=0.7, k=1024, r=20, T=15,
                             block=65536, steps=1, warm=1),
+    # Table 1's synthetic row (Section 4): d = n = 100,000, A = B = G D (G Gaussian, D_ii = 1 / i), k = 2,000, the
+    # default r = 5, T = 10, m = 4 n r ln n; SMP-PCA against LELA and the optimum, with the paper's printed errors
+    "table1": dict(d=100_000, n1=100_000, n2=100_000, k=2000, r=5, T=10, block=16384,
+                   paper={"optimal": 0.0271, "lela": 0.0274, "smp_pca": 0.0280}),
     # batched form: 256 FP32 instances (n in [64, 2048], d in [1e4, 5e5], r in {5, 10, 20}, k = 8 r) solved
     # together, sketch engine per (k, n bucket) from the autotuner
     "batch": dict(instances=256, warm=16, block=65536, pool_rows=1_000_000, width=2048, L=20, sigma=0.1, alpha=0.5,
@@ -202,6 +206,7 @@ def main():
     ap.add_argument("--no-error", action="store_true")
     ap.add_argument("--workers", type=int, default=0, help="solve worker threads of the batched / serving forms")
     ap.add_argument("--batch-dtype", default="f32", choices=["f32", "bf16"], help="stored inputs of the batched form")
+    ap.add_argument("--size", type=int, default=0, help="table1 workload: d = n = SIZE instead of 100,000")
     ap.add_argument("--no-baseline", action="store_true",
                     help="skip the SVD(A~^T B~) and multinomial-sampling comparisons")
     args = ap.parse_args()
@@ -214,6 +219,8 @@ def main():
         return run_batched(args, w)
     if args.workload in ("precision", "precision_block"):
         return run_precision(args, w)
+    if args.workload == "table1":
+        return run_table1(args, w)
 
     import torch
     import torch.distributed as dist
@@ -347,15 +354,70 @@ def main():
         mn = {"name": "row-wise multinomial sampling (smp_sample_multinomial)", "sample_ms": ms_m,
               "bernoulli_sample_ms": ms_b, "nnz": int(nnz_m), "bernoulli_nnz": int(nnz_b), "spectral_err": None}
 
+    # LELA, the two-pass method of Table 1, on the same data: pass 1 norms only, the same Omega sampling, pass 2 the
+    # exact entries on tensor cores, the same WAltMin (outside the timed region; per-block CUDA events on the passes,
+    # host wall time around whole solves, which synchronise)
+    lela = None
+    if rank == 0 and not args.no_baseline:
+        ls = pipeline.Solver(w["n1"], w["n2"], 16, torch.float32, seed=1 + rank, max_rows=w["block"])
+
+        def lela_solve(evn=None, evx=None):
+            smp.smp_sketch_reset(ls.ctx)
+            for r0 in range(0, w["d"], w["block"]):
+                r1 = min(w["d"], r0 + w["block"])
+                ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                ev[0].record(stream)
+                smp.smp_norms_accumulate(ls.ctx, A[r0:r1], w["n1"], B[r0:r1], w["n2"], r0, r1 - r0)
+                ev[1].record(stream)
+                if evn is not None:
+                    evn.append(ev)
+            smp.smp_sketch_finalize(ls.ctx)
+            nnz_l = ls.sample(m, 2 + rank)
+            for r0 in range(0, w["d"], w["block"]):
+                r1 = min(w["d"], r0 + w["block"])
+                ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                ev[0].record(stream)
+                smp.smp_exact_accumulate(ls.ctx, A[r0:r1], w["n1"], B[r0:r1], w["n2"], r0, r1 - r0)
+                ev[1].record(stream)
+                if evx is not None:
+                    evx.append((ev[0], ev[1], r1 - r0))
+            vals_l = torch.empty(max(nnz_l, 1), dtype=torch.float32, device=dev)
+            smp.smp_exact_values(ls.ctx, vals_l)
+            return ls.waltmin(vals_l[:nnz_l], w["r"], w["T"], 0, 3 + rank), nnz_l
+
+        lela_solve()
+        torch.cuda.synchronize()
+        evn, evx, reps = [], [], 2
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            (Ul, Sl, Vl), nnz_l = lela_solve(evn, evx)
+        torch.cuda.synchronize()
+        l_ms = 1e3 * (time.perf_counter() - t0) / reps
+        n_ms = sum(a.elapsed_time(b) for a, b in evn) / reps
+        x_ms = [a.elapsed_time(b) for a, b, _ in evx]
+        x_rows = sum(n for _, _, n in evx) / len(evx)
+        x_flops = 2.0 * w["n1"] * w["n2"] * x_rows             # the dense tile product per launch
+        tf32_peak = peaks["bf16_tflops"] * (1.1 / 2.25)
+        x_avg = sum(x_ms) / len(x_ms) / 1e3
+        lela = {"name": "LELA two-pass (smp_norms_accumulate; smp_exact_accumulate: transpose_tf32_kernel + "
+                        "exact_tc_kernel)", "solves_per_s": 1e3 / l_ms, "ms": l_ms, "nnz": int(nnz_l),
+                "norms_pass_ms": n_ms, "norms_pass_gbs": w["d"] * ntot * 4 / (n_ms / 1e3) / 1e9,
+                "exact_pass_ms": sum(x_ms) / reps, "exact_launch_ms": x_avg * 1e3,
+                "exact_tflops": x_flops / x_avg / 1e12, "exact_tf32_frac": x_flops / x_avg / 1e12 / tf32_peak,
+                "exact_useful_tflops": 2.0 * nnz_l * x_rows / x_avg / 1e12, "spectral_err": None}
+        ls.close()
+
     err, opt_err = None, None
     if not args.no_error and rank == 0:
-        extra = ([(Ub, Sb, Vb)] if base else []) + ([(Um, Sm, Vm)] if mn else [])
+        extra = ([(Ub, Sb, Vb)] if base else []) + ([(Um, Sm, Vm)] if mn else []) + ([(Ul, Sl, Vl)] if lela else [])
         errs, opt_err = spectral_error(torch, A, B, [(U, S, V)] + extra)
         err = errs[0]
         if base:
             base["spectral_err"] = errs[1]
         if mn:
-            mn["spectral_err"] = errs[-1]
+            mn["spectral_err"] = errs[1 + (1 if base else 0)]
+        if lela:
+            lela["spectral_err"] = errs[-1]
 
     # ---- end to end: host-resident inputs copied in every step (pinned, double-buffered row blocks)
     e2e = None
@@ -383,7 +445,7 @@ def main():
                 "p50_ms": statistics.median(step_ms), "p99_ms": step_ms[min(len(step_ms) - 1,
                                                                             int(math.ceil(0.99 * len(step_ms))) - 1)],
                 "sketch_gbs": roof["hbm_gbs"], "spectral_err": err, "optimal_err": opt_err,
-                "baseline_sketch_svd": base, "sampler_multinomial": mn,
+                "baseline_sketch_svd": base, "sampler_multinomial": mn, "lela": lela,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk}
         print(json.dumps(line), flush=True)
@@ -391,6 +453,84 @@ def main():
         dist.barrier()
         dist.destroy_process_group()
     solver.close()
+
+
+def implicit_errors(torch, A, factors, r, iters=40, block=16, seed=0):
+    """For the implicit symmetric product M = A^T A (never formed): ||M - U S V^T||_2 / ||M||_2 for each (U, S, V)
+    and the Eckart-Young optimum sigma_{r+1} / sigma_1, by block subspace iteration with a Rayleigh-Ritz step (torch
+    FP32 products without TF32, binary64 Ritz problems). Evaluation only."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    g = torch.Generator(device=A.device)
+    g.manual_seed(seed)
+    n = A.shape[1]
+
+    def mul(X):
+        return A.T @ (A @ X)
+
+    def top_eigs(op, b):
+        X = torch.linalg.qr(torch.randn(n, b, generator=g, device=A.device))[0]
+        for _ in range(iters):
+            X = torch.linalg.qr(op(X))[0]
+        H = (X.T @ op(X)).double()
+        return torch.linalg.eigvalsh(0.5 * (H + H.T)).flip(0)
+
+    ev = top_eigs(mul, block)
+    s1 = float(ev[0])
+    opt = float(ev[r] / ev[0])
+    errs = []
+    for U, S, V in factors:
+        Uf, Vf, Sf = U.float(), V.float(), S.float()
+
+        def rtr(X, Uf=Uf, Vf=Vf, Sf=Sf):   # R^T R X with R = M - U S V^T (M symmetric)
+            Y = mul(X) - Uf @ (Sf[:, None] * (Vf.T @ X))
+            return mul(Y) - Vf @ (Sf[:, None] * (Uf.T @ Y))
+
+        errs.append(float(torch.sqrt(torch.clamp(top_eigs(rtr, 8)[0], min=0.0))) / s1)
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    return errs, opt
+
+
+def run_table1(args, w):
+    """Table 1's synthetic row (Section 4): SMP-PCA (one pass: Gaussian sketch with k = 2,000, above the tensor-core
+    engines' limits, so on the CUDA cores) and LELA (two passes: norms, then the exact entries on tensor cores) on
+    the same A = B = G D, their relative spectral errors and the optimum next to the paper's printed values, and
+    each solve's wall time (both end in a synchronising WAltMin)."""
+    import torch
+    from paper_1610_06656_gb300 import build, pipeline, smp, synth
+    smp.load(build.build())
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    if args.size:
+        w = dict(w, d=args.size, n1=args.size, n2=args.size)
+    n = w["n1"]
+    A = synth.gd_torch(w["d"], n, seed=2016, device=dev)
+    torch.cuda.synchronize()
+    m = pipeline.default_m(n, n, w["r"])
+    out = {}
+    for name, k in (("smp_pca", w["k"]), ("lela", 16)):
+        s = pipeline.Solver(n, n, k, torch.float32, seed=1, same_ab=True, max_rows=w["block"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if name == "smp_pca":
+            res = s.solve(A, None, w["r"], w["T"], m=m, sample_seed=2, walt_seed=3, block_rows=w["block"])
+        else:
+            res = s.lela(A, None, w["r"], w["T"], m=m, sample_seed=2, walt_seed=3, block_rows=w["block"])
+        torch.cuda.synchronize()
+        out[name] = dict(ms=1e3 * (time.perf_counter() - t0), nnz=int(res["nnz"]),
+                         factors=(res["U"], res["S"], res["V"]))
+        s.close()
+    errs, opt = implicit_errors(torch, A, [out["smp_pca"]["factors"], out["lela"]["factors"]], w["r"])
+    line = {"metric": "relative spectral error, Table 1 synthetic row", "value": errs[0],
+            "unit": "||A^T B - U S V^T||_2 / ||A^T B||_2", "higher_is_better": False, "n_gpus": 1,
+            "vs_baseline": None, "dtype": "f32 (SMP-PCA sketch on CUDA cores), tf32 (LELA exact entries)",
+            "data": "synthetic A = B = G D, G standard Gaussian (torch RNG, seed 2016), D_ii = 1 / i",
+            "config": {"workload": "table1", "d": w["d"], "n": n, "k": w["k"], "r": w["r"], "T": w["T"],
+                       "m": m, "block_rows": w["block"]},
+            "smp_pca": {"spectral_err": errs[0], "solve_ms": out["smp_pca"]["ms"], "nnz": out["smp_pca"]["nnz"]},
+            "lela": {"spectral_err": errs[1], "solve_ms": out["lela"]["ms"], "nnz": out["lela"]["nnz"]},
+            "optimal_err": opt, "paper_table1": w["paper"]}
+    print(json.dumps(line), flush=True)
 
 
 def run_serving(args, w):

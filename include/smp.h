@@ -87,7 +87,7 @@ typedef enum {
 typedef struct {
     int64_t n1;            /* columns of A (>= 1)                                                             */
     int64_t n2;            /* columns of B (>= 1); must equal n1 when same_ab                                  */
-    int32_t k;             /* sketch size, 1 <= k <= 1024                                                      */
+    int32_t k;             /* sketch size, 1 <= k <= 4096 (tensor-core engines: k <= 512 TF32, 1024 BF16 / FP8) */
     int32_t dtype;         /* smp_dtype of the row blocks                                                      */
     uint64_t seed;         /* Pi seed: Philox key (seed mod 2^32, seed >> 32)                                  */
     int32_t same_ab;       /* 1: B is A (PCA, Section 3 Remark 3); B pointers are ignored and Bt aliases At     */

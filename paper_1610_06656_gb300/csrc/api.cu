@@ -164,7 +164,7 @@ smp_status smp_sketch_begin(const smp_params* params, void* stream, smp_ctx** ou
     if (p.n1 < 1 || p.n2 < 1 || p.n1 > (int64_t)1 << 30 || p.n2 > (int64_t)1 << 30)
         return fail(nullptr, SMP_EINVAL, "n1, n2 must be in [1, 2^30]");
     if (p.same_ab && p.n1 != p.n2) return fail(nullptr, SMP_EINVAL, "same_ab needs n1 == n2");
-    if (p.k < 1 || p.k > 1024) return fail(nullptr, SMP_EINVAL, "k must be in [1, 1024]");
+    if (p.k < 1 || p.k > 4096) return fail(nullptr, SMP_EINVAL, "k must be in [1, 4096]");
     if (p.engine < SMP_ENGINE_AUTO || p.engine > SMP_ENGINE_SRHT) return fail(nullptr, SMP_EINVAL, "unknown engine");
     if (p.engine == SMP_ENGINE_SRHT) {
         if (p.dtype != SMP_F32) return fail(nullptr, SMP_EUNSUPPORTED, "SMP_ENGINE_SRHT takes SMP_F32 row blocks");

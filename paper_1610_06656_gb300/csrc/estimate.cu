@@ -53,6 +53,25 @@ __global__ void __launch_bounds__(256) estimate_kernel(const T* __restrict__ At,
     }
 }
 
+// k > 1024: the same sums without caching At_i in registers (lanes stride over the sketch rows).
+template <typename T>
+__global__ void __launch_bounds__(256) estimate_long_kernel(const T* __restrict__ At, const T* __restrict__ Bt,
+                                                            int64_t ldk, int k, const double* __restrict__ DA,
+                                                            const double* __restrict__ DB,
+                                                            const int32_t* __restrict__ erow,
+                                                            const int32_t* __restrict__ col, int64_t nnz, T* vals) {
+    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (p >= nnz) return;
+    const int64_t i = erow[p], j = col[p];
+    const T* ai = At + i * ldk;
+    const T* bj = Bt + j * ldk;
+    T s = T(0);
+    for (int idx = lane; idx < k; idx += 32) s = fma(ai[idx], bj[idx], s);
+    s = warp_sum(s);
+    if (lane == 0) vals[p] = (T)(DA[i] * DB[j] * (double)s);
+}
+
 template <typename T, int NPL>
 void launch_npl(smp_ctx* c, void* vals) {
     const T* At = (const T*)c->sk;
@@ -71,7 +90,14 @@ void launch_typed(smp_ctx* c, void* vals) {
     if (k <= 128) launch_npl<T, 4>(c, vals);
     else if (k <= 256) launch_npl<T, 8>(c, vals);
     else if (k <= 512) launch_npl<T, 16>(c, vals);
-    else launch_npl<T, 32>(c, vals);
+    else if (k <= 1024) launch_npl<T, 32>(c, vals);
+    else {
+        const T* At = (const T*)c->sk;
+        const T* Bt = c->p.same_ab ? At : At + c->p.n1 * c->ldk;
+        const double* DB = c->p.same_ab ? c->D_all : c->D_all + c->p.n1;
+        estimate_long_kernel<T><<<smp::counted((unsigned)((c->nnz * 32 + 255) / 256)), 256, 0, c->stream>>>(
+            At, Bt, c->ldk, k, c->D_all, DB, c->erow, c->col, c->nnz, (T*)vals);
+    }
 }
 
 }  // namespace

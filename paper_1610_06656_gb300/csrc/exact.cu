@@ -60,56 +60,96 @@ __device__ __forceinline__ float load_as(const float* p, float) { return __ldcs(
 __device__ __forceinline__ float load_as(const __nv_bfloat16* p, float) { return __bfloat162float(*p); }
 __device__ __forceinline__ double load_as(const double* p, double) { return __ldcs(p); }
 
-constexpr int NRM_COLS = 64;     // columns per CTA (two warps side by side)
-constexpr int NRM_GROUPS = 4;    // row groups per CTA (thread (column tid % 64, group tid / 64))
-constexpr int NRM_UNROLL = 8;    // loads in flight per thread
+// Four consecutive elements (16 bytes of binary32, 8 of BF16, 32 of binary64) when the group is aligned and whole.
+__device__ __forceinline__ void load4(const float* p, float (&x)[4]) {
+    const float4 v = __ldcs((const float4*)p);
+    x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+}
+__device__ __forceinline__ void load4(const __nv_bfloat16* p, float (&x)[4]) {
+    const uint2 v = __ldcs((const uint2*)p);
+    x[0] = __uint_as_float(v.x << 16), x[1] = __uint_as_float(v.x & 0xFFFF0000u);
+    x[2] = __uint_as_float(v.y << 16), x[3] = __uint_as_float(v.y & 0xFFFF0000u);
+}
+__device__ __forceinline__ void load4(const double* p, double (&x)[4]) {
+    const double2 a = __ldcs((const double2*)p), b = __ldcs((const double2*)p + 1);
+    x[0] = a.x, x[1] = a.y, x[2] = b.x, x[3] = b.y;
+}
 
+constexpr int NRM_COLS = 128;    // columns per CTA: lane l of every warp owns columns 4 l .. 4 l + 3
+constexpr int NRM_WARPS = 8;     // warp w reads rows rs + w, rs + w + 8, ...
+constexpr int NRM_UNROLL = 8;    // rows in flight per thread
+
+// Column tiles cover A's columns, then B's (a tile never straddles the two). vec: every four-column group that
+// lies inside its matrix starts on an element-vector boundary (aligned base, ld a multiple of 4).
 template <typename TIn, typename TAcc>
 __global__ void __launch_bounds__(256) norms_kernel(const TIn* __restrict__ A, int64_t lda, const TIn* __restrict__ B,
-                                                    int64_t ldb, int64_t n1, int64_t ntot, int64_t nrows,
-                                                    int64_t rows_per_split, double* __restrict__ nsq) {
-    __shared__ double red[NRM_GROUPS][NRM_COLS];
-    const int tid = threadIdx.x, cl = tid % NRM_COLS, g = tid / NRM_COLS;
-    const int64_t c = (int64_t)blockIdx.x * NRM_COLS + cl;
+                                                    int64_t ldb, int64_t n1, int64_t n2, int tiles_a, int64_t nrows,
+                                                    int64_t rows_per_split, int64_t ntot, bool vec,
+                                                    double* __restrict__ nsq) {
+    __shared__ double red[NRM_WARPS][NRM_COLS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool on_b = (int)blockIdx.x >= tiles_a;
+    const int64_t c0 = (int64_t)(on_b ? blockIdx.x - tiles_a : blockIdx.x) * NRM_COLS + 4 * lane;
+    const int64_t n = on_b ? n2 : n1;
+    const TIn* src = (on_b ? B : A) + c0;
+    const int64_t ld = on_b ? ldb : lda;
     const int split = blockIdx.y;
     const int64_t rs = (int64_t)split * rows_per_split, re = min(nrows, rs + rows_per_split);
-    const bool valid = c < ntot;
-    const TIn* src = !valid ? A : (c < n1 ? A + c : B + (c - n1));
-    const int64_t ld = c < n1 ? lda : ldb;
-    TAcc hi = TAcc(0), lo = TAcc(0);
-    if (valid) {
-        int64_t t = rs + g;
-        for (; t + (NRM_UNROLL - 1) * NRM_GROUPS < re; t += NRM_UNROLL * NRM_GROUPS) {
-            TAcc x[NRM_UNROLL];
+    const int nv = (int)max((int64_t)0, min((int64_t)4, n - c0));   // valid columns of this lane's group
+    TAcc hi[4] = {TAcc(0), TAcc(0), TAcc(0), TAcc(0)}, lo[4] = {TAcc(0), TAcc(0), TAcc(0), TAcc(0)};
+    if (nv == 4 && vec) {
+        int64_t t = rs + warp;
+        for (; t + (NRM_UNROLL - 1) * NRM_WARPS < re; t += NRM_UNROLL * NRM_WARPS) {
+            TAcc x[NRM_UNROLL][4];
 #pragma unroll
-            for (int u = 0; u < NRM_UNROLL; ++u) x[u] = load_as(src + (t + u * NRM_GROUPS) * ld, TAcc(0));
+            for (int u = 0; u < NRM_UNROLL; ++u) load4(src + (t + u * NRM_WARPS) * ld, x[u]);
 #pragma unroll
-            for (int u = 0; u < NRM_UNROLL; ++u) sq_add(x[u], hi, lo);
+            for (int u = 0; u < NRM_UNROLL; ++u)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) sq_add(x[u][q], hi[q], lo[q]);
         }
-        for (; t < re; t += NRM_GROUPS) sq_add(load_as(src + t * ld, TAcc(0)), hi, lo);
-    }
-    red[g][cl] = (double)hi + (double)lo;
-    __syncthreads();
-    if (g == 0 && valid) {
-        double v = red[0][cl];
+        for (; t < re; t += NRM_WARPS) {
+            TAcc x[4];
+            load4(src + t * ld, x);
 #pragma unroll
-        for (int q = 1; q < NRM_GROUPS; ++q) v += red[q][cl];
-        nsq[(int64_t)split * ntot + c] += v;
+            for (int q = 0; q < 4; ++q) sq_add(x[q], hi[q], lo[q]);
+        }
+    } else if (nv > 0) {
+        for (int64_t t = rs + warp; t < re; t += NRM_WARPS)
+            for (int q = 0; q < nv; ++q) sq_add(load_as(src + t * ld + q, TAcc(0)), hi[q], lo[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red[warp][4 * lane + q] = (double)hi[q] + (double)lo[q];
+    __syncthreads();
+    if (threadIdx.x < NRM_COLS) {
+        const int cl = threadIdx.x;
+        const int64_t col = (int64_t)(on_b ? blockIdx.x - tiles_a : blockIdx.x) * NRM_COLS + cl;
+        if (col < n) {
+            double v = red[0][cl];
+#pragma unroll
+            for (int w = 1; w < NRM_WARPS; ++w) v += red[w][cl];
+            nsq[(int64_t)split * ntot + (on_b ? n1 + col : col)] += v;
+        }
     }
 }
 
 template <typename TIn, typename TAcc>
 cudaError_t launch_norms_typed(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t nrows) {
-    const int64_t ntot = c->ntot;
-    const int tiles = (int)((ntot + NRM_COLS - 1) / NRM_COLS);
-    // row splits: enough CTAs for about four per SM, at most the context's partial buffers
-    int splits = (int)std::max<int64_t>(1, (4 * (int64_t)c->sm_count + tiles - 1) / tiles);
-    splits = (int)std::min<int64_t>(std::min(splits, c->splits), std::max<int64_t>(1, nrows / (NRM_GROUPS * 8)));
+    const bool same = c->p.same_ab;
+    const int64_t n1 = c->p.n1, n2 = same ? 0 : c->p.n2;
+    const int tiles_a = (int)((n1 + NRM_COLS - 1) / NRM_COLS);
+    const int tiles = tiles_a + (int)((n2 + NRM_COLS - 1) / NRM_COLS);
+    const size_t vbytes = 4 * sizeof(TIn);
+    auto aligned = [&](const void* p, int64_t ld) { return (uintptr_t)p % vbytes == 0 && ld % 4 == 0; };
+    const bool vec = aligned(A, lda) && (same || aligned(B, ldb));
+    // row splits: about two CTAs per SM, at most the context's partial buffers, at least 64 rows each
+    int splits = (int)std::max<int64_t>(1, (2 * (int64_t)c->sm_count + tiles - 1) / tiles);
+    splits = (int)std::min<int64_t>(std::min(splits, c->splits), std::max<int64_t>(1, nrows / 64));
     const int64_t rps = (nrows + splits - 1) / splits;
     splits = (int)((nrows + rps - 1) / rps);
     norms_kernel<TIn, TAcc><<<smp::counted(dim3((unsigned)tiles, (unsigned)splits)), 256, 0, c->stream>>>(
-        (const TIn*)A, lda, c->p.same_ab ? (const TIn*)A : (const TIn*)B, c->p.same_ab ? lda : ldb, c->p.n1, ntot,
-        nrows, rps, c->nsq);
+        (const TIn*)A, lda, same ? (const TIn*)A : (const TIn*)B, same ? lda : ldb, n1, n2, tiles_a, nrows, rps,
+        c->ntot, vec, c->nsq);
     return cudaGetLastError();
 }
 

@@ -72,6 +72,25 @@ def lowrank_plus_noise_torch(d, n1, n2, L, sigma, alpha, seed, device, dtype=Non
     return A, B, Z, X, Y
 
 
+def gd(d, n, seed, dtype=np.float64):
+    """Section 4's synthetic matrices: G D with G (d x n) standard Gaussian and D_ii = 1 / i (i from 1)."""
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal((d, n)) / np.arange(1, n + 1)).astype(dtype)
+
+
+def gd_torch(d, n, seed, device, block_rows=8192):
+    """Device-side G D (binary32, torch RNG seeded), generated in row blocks to bound temporary memory."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    dscale = 1.0 / torch.arange(1, n + 1, device=device, dtype=torch.float32)
+    A = torch.empty(d, n, device=device, dtype=torch.float32)
+    for r0 in range(0, d, block_rows):
+        r1 = min(d, r0 + block_rows)
+        A[r0:r1] = torch.randn(r1 - r0, n, generator=g, device=device, dtype=torch.float32) * dscale
+    return A
+
+
 def cone(d, n1, n2, theta, seed, dtype=np.float64):
     """A (d x n1) and B (d x n2) with unit columns at angle phi ~ U[0, theta] from one shared random direction."""
     rng = np.random.default_rng(seed)

@@ -120,6 +120,33 @@ def test_sketch_simt_f64(env, data):
     s.close()
 
 
+@pytest.mark.parametrize("dtype_name", ["f32", "f64"])
+def test_long_sketch_above_1024(env, dtype_name):
+    """k = 2,000 (Table 1's sketch size; above the tensor-core engines' limits): the CUDA-core sketch and the
+    estimate's long-sketch kernel against the oracle, 400 rows in 150-row blocks, n1 = 70, n2 = 50."""
+    torch, smp, pipeline = env
+    npdt = np.float32 if dtype_name == "f32" else np.float64
+    A, B = synth.lowrank_plus_noise(400, 70, 50, 5, 0.1, 0.5, seed=8, dtype=npdt)
+    tdt = torch.float32 if dtype_name == "f32" else torch.float64
+    k = 2000
+    s = pipeline.Solver(70, 50, k, tdt, seed=13, max_rows=150)
+    s.sketch(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), 150)
+    st = s.sketch_state()
+    ref = O.sketch(A, B, k, 13, block_rows=150)
+    tol = 2e-5 if dtype_name == "f32" else 1e-12
+    assert _colrel(st["At"].cpu().numpy().astype(np.float64), ref.At.T) < tol
+    assert _colrel(st["Bt"].cpu().numpy().astype(np.float64), ref.Bt.T) < tol
+    m = O.default_m(70, 50, 3)
+    nnz = s.sample(m, seed=4)
+    vals = s.estimate(nnz).cpu().numpy().astype(np.float64)
+    om = omega_numpy(s)
+    rows, cols = csr_rows(om["row_ptr"]), om["col"]
+    want = O.estimate(rows, cols, ref.At, ref.Bt, ref.sA, ref.sB)
+    scale = np.sqrt(ref.sA[rows] * ref.sB[cols])
+    assert np.max(np.abs(vals - want) / scale) < (2e-5 if dtype_name == "f32" else 1e-11)
+    s.close()
+
+
 def test_sketch_identity_pi_is_exact(env):
     """Pi = I (k = d) through the explicit-Pi hook: At = A bit for bit, so M~ = A^T B exactly."""
     torch, smp, pipeline = env
