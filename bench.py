@@ -49,7 +49,7 @@ WORKLOADS = {
     # batched form: 256 FP32 instances (n in [64, 2048], d in [1e4, 5e5], r in {5, 10, 20}, k = 8 r) solved
     # together, sketch engine per (k, n bucket) from the autotuner
     "batch": dict(instances=256, warm=16, block=65536, pool_rows=1_000_000, width=2048, L=20, sigma=0.1, alpha=0.5,
-                  budget=200e9, workers=8, T=10),
+                  budget=200e9, workers=16, T=10),
 }
 
 
@@ -700,7 +700,8 @@ def run_batched(args, w):
             "vs_baseline": None, "dtype": ("bf16" if bf16 else "tf32/f32") + " per instance (autotuned)",
             "data": "synthetic (low rank 20 + noise 0.1, column scales (j+1)^-0.5); instance inputs are windows of a "
                     "resident %d x %d %s pool pair" % (w["pool_rows"], w["width"], "BF16" if bf16 else "FP32"),
-            "config": {"workload": "batch", "instances": w["instances"], "n": "uniform [64, 2048]",
+            "config": {"workload": "batch", "schedule": "staged: a budget-sized wave's sketches, then its solve chains",
+                       "instances": w["instances"], "n": "uniform [64, 2048]",
                        "d": "uniform [10000, 500000]", "r": [5, 10, 20], "k": "8 r", "T": w["T"],
                        "block_rows": w["block"], "solve_workers": workers, "engines": engines,
                        "autotune_s": t_tune, "autotune_trials": tuner.trials},

@@ -103,11 +103,16 @@ def probe_timer(pool_A, pool_B, rows=32768, reps=3):
     return time_fn
 
 
-def run(server, specs, pool_A, pool_B, dtype, tuner, block_rows=65536, keep=None):
-    """Tune each instance's engine, then solve all instances together (every arrival at time zero). Returns the
-    server's per-instance records and the wall time from start to the last completion. keep: optional
-    {idx: (U, S, V) device tensors} to receive those instances' factors."""
+def run(server, specs, pool_A, pool_B, dtype, tuner, block_rows=65536, keep=None, staged=True):
+    """Tune each instance's engine, then solve all instances together (every arrival at time zero). staged: the
+    sketches of a budget-sized wave first, then its solve chains (serve.run_staged); otherwise the streaming
+    server loop. Returns the server's per-instance records and the wall time from start to the last completion.
+    keep: optional {idx: (U, S, V) device tensors} to receive those instances' factors."""
     for sp in specs:
         sp.engine = tuner.choose(sp.n, sp.k, dtype)
         sp.arrival = 0.0
+    if staged:
+        import torch
+        return serve.run_staged(server, specs, pool_A, pool_B, dtype, block_rows=block_rows, keep=keep,
+                                sync=torch.cuda.synchronize)
     return serve.run(server, specs, pool_A, pool_B, dtype, block_rows=block_rows, keep=keep)

@@ -121,3 +121,47 @@ def run(server, jobs, pool_A, pool_B, dtype, block_rows=32768, engine=S.SMP_ENGI
     first = min(j.arrival for j in jobs) if jobs else 0.0
     wall = (max(r["done_at"] for r in records) - first) if records else 0.0
     return records, wall
+
+
+def run_staged(server, jobs, pool_A, pool_B, dtype, block_rows=32768, engine=S.SMP_ENGINE_AUTO, keep=None,
+               time_limit=600.0, sync=None):
+    """Batched schedule, stage by stage: admit as many jobs as the budget takes (a wave), push every block of the
+    wave (all sketches run concurrently), wait until the device has finished them (sync()), then close the whole
+    wave so the server's workers run the solve chains without sketch kernels queued in front of them on the
+    device's hardware queues; collect, then the next wave. Returns records and wall time like run()."""
+    pending = collections.deque(jobs)
+    records = []
+    lda = pool_A.stride(0)
+    t0 = time.perf_counter()
+    while pending:
+        if time.perf_counter() - t0 > time_limit:
+            raise RuntimeError("batched run exceeded %.0f s" % time_limit)
+        wave = []
+        while pending:
+            jid = S.smp_serve_admit(server, pending[0].params(dtype, engine, block_rows))
+            if jid is None:
+                break
+            wave.append((jid, pending.popleft()))
+        if not wave:
+            raise RuntimeError("a single job does not fit the server's memory budget")
+        plans = [block_plan(spec.d, block_rows) for _, spec in wave]
+        for p in range(max(len(pl) for pl in plans)):
+            for (jid, spec), pl in zip(wave, plans):
+                if p < len(pl):
+                    r0, nr = pl[p]
+                    a = pool_A[spec.row_offset + r0: spec.row_offset + r0 + nr, :spec.n]
+                    b = pool_B[spec.row_offset + r0: spec.row_offset + r0 + nr, :spec.n]
+                    S.smp_serve_block(server, jid, a, lda, b, lda, r0, nr)
+        if sync is not None:
+            sync()
+        for jid, _ in wave:
+            S.smp_serve_close(server, jid)
+        for jid, spec in wave:
+            U = Sv = V = None
+            if keep is not None and spec.idx in keep:
+                U, Sv, V = keep[spec.idx]
+            nnz, lat = S.smp_serve_collect(server, jid, U, Sv, V)
+            records.append(dict(idx=spec.idx, latency_ms=lat, nnz=nnz, done_at=time.perf_counter() - t0))
+    wall = max(r["done_at"] for r in records) if records else 0.0
+    return records, wall
+
