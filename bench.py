@@ -240,30 +240,54 @@ def main():
     A, B, _, _, _ = synth.lowrank_plus_noise_torch(w["d"], w["n1"], w["n2"], w["L"], w["sigma"], w["alpha"],
                                                   seed=1001 + rank, device=dev)
     torch.cuda.synchronize()
-    solver = pipeline.Solver(w["n1"], w["n2"], w["k"], torch.float32, seed=1 + rank, engine=engine,
-                             max_rows=w["block"])
+    # two contexts on streams of their own: consecutive solves alternate between them, so that the sketch of solve
+    # i + 1 (tensor-bound) runs while solve i's WAltMin (small dependent launches and host checks) finishes
+    streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+    solvers = [pipeline.Solver(w["n1"], w["n2"], w["k"], torch.float32, seed=1 + rank, engine=engine,
+                               max_rows=w["block"], stream=st.cuda_stream) for st in streams]
+    solver = solvers[0]
     m = pipeline.default_m(w["n1"], w["n2"], w["r"])
 
-    def sketch_timed(evs):
-        smp.smp_sketch_reset(solver.ctx)
+    def sketch_timed(i, evs):
+        sv, st = solvers[i % 2], streams[i % 2]
+        smp.smp_sketch_reset(sv.ctx)
         for r0 in range(0, w["d"], w["block"]):
             r1 = min(w["d"], r0 + w["block"])
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            smp.smp_sketch_accumulate(solver.ctx, A[r0:r1], w["n1"], B[r0:r1], w["n2"], r0, r1 - r0)
-            e1.record(stream)
+            e0.record(st)
+            smp.smp_sketch_accumulate(sv.ctx, A[r0:r1], w["n1"], B[r0:r1], w["n2"], r0, r1 - r0)
+            e1.record(st)
             evs.append((e0, e1, r1 - r0))
-        smp.smp_sketch_finalize(solver.ctx)
+        smp.smp_sketch_finalize(sv.ctx)
 
-    def step(evs):
-        sketch_timed(evs)
-        nnz = solver.sample(m, 2 + rank)
-        vals = solver.estimate(nnz)
-        return solver.waltmin(vals, w["r"], w["T"], 0, 3 + rank), nnz
+    def run_steps(count, evs, step_events):
+        """count solves, pipelined: solve i's sketch was issued before solve i - 1's WAltMin."""
+        out = None
+        marks = {}
 
-    for _ in range(args.warmup):
-        step([])
+        def issue(i):
+            s0 = torch.cuda.Event(enable_timing=True)
+            s0.record(streams[i % 2])
+            marks[i] = s0
+            sketch_timed(i, evs)
+
+        issue(0)
+        for i in range(count):
+            sv, st = solvers[i % 2], streams[i % 2]
+            nnz = sv.sample(m, 2 + rank)
+            with torch.cuda.stream(st):
+                vals = sv.estimate(nnz)
+            if i + 1 < count:
+                issue(i + 1)
+            with torch.cuda.stream(st):
+                out = sv.waltmin(vals, w["r"], w["T"], 0, 3 + rank), nnz
+            s1 = torch.cuda.Event(enable_timing=True)
+            s1.record(st)
+            step_events.append((marks.pop(i), s1))
+        return out
+
+    run_steps(args.warmup, [], [])
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
@@ -276,13 +300,13 @@ def main():
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
-    for _ in range(args.steps):
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        (U, S, V), nnz = step(sk_events)
-        s1.record(stream)
-        step_events.append((s0, s1))
+    for st in streams:
+        st.wait_event(t_start)
+    (U, S, V), nnz = run_steps(args.steps, sk_events, step_events)
+    for st in streams:
+        ev = torch.cuda.Event()
+        ev.record(st)
+        stream.wait_event(ev)
     t_end.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -422,7 +446,8 @@ def main():
     # ---- end to end: host-resident inputs copied in every step (pinned, double-buffered row blocks)
     e2e = None
     if args.e2e_steps > 0:
-        e2e = run_e2e(torch, smp, solver, A, B, w, m, rank, args.e2e_steps, stream, world, dev)
+        with torch.cuda.stream(streams[0]):
+            e2e = run_e2e(torch, smp, solver, A, B, w, m, rank, args.e2e_steps, streams[0], world, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -441,6 +466,7 @@ def main():
                 "data": "synthetic (low rank 20 + noise 0.1, column scales (j+1)^-0.5, torch RNG seeded per rank)",
                 "config": {"workload": args.workload, **{k: w[k] for k in ("d", "n1", "n2", "k", "r", "T")},
                            "block_rows": w["block"], "m": m, "nnz": int(nnz), "parallelism": "replicas",
+                           "pipelining": "2 contexts on 2 streams: solve i + 1's sketch overlaps solve i's WAltMin",
                            "l2": l2_note, "engine": args.engine},
                 "p50_ms": statistics.median(step_ms), "p99_ms": step_ms[min(len(step_ms) - 1,
                                                                             int(math.ceil(0.99 * len(step_ms))) - 1)],
@@ -452,7 +478,8 @@ def main():
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
-    solver.close()
+    for sv in solvers:
+        sv.close()
 
 
 def implicit_errors(torch, A, factors, r, iters=40, block=16, seed=0):
