@@ -717,9 +717,9 @@ def run_batched(args, w):
     peaks, peak_kind = measured_peaks()
     streamed = sum(sp.d * 2 * sp.n * esz for sp in specs)
     engines = {}
+    names = {smp.SMP_ENGINE_SIMT: "simt", smp.SMP_ENGINE_TC: "tc", smp.SMP_ENGINE_TC_FP8: "tc_fp8"}
     for sp in specs:
-        engines[{smp.SMP_ENGINE_SIMT: "simt", smp.SMP_ENGINE_TC: "tc"}.get(sp.engine, str(sp.engine))] = \
-            engines.get({smp.SMP_ENGINE_SIMT: "simt", smp.SMP_ENGINE_TC: "tc"}.get(sp.engine, str(sp.engine)), 0) + 1
+        engines[names.get(sp.engine, str(sp.engine))] = engines.get(names.get(sp.engine, str(sp.engine)), 0) + 1
     lat = sorted(r["latency_ms"] for r in records)
     line = {"metric": "batched: instances solved per second (256 uneven instances together)",
             "value": len(records) / wall, "unit": "solves/s", "n_gpus": 1, "steps": len(records), "warmup": w["warm"],

@@ -38,11 +38,13 @@ def n_bucket(n):
 
 
 class EngineTuner:
-    """Per (dtype, k, n bucket): time every candidate engine with time_fn(n, k, dtype, engine) -> ms per block
-    (None when the engine cannot run the shape) and keep the fastest. Results are cached in memory and, with
+    """Per (dtype, k, n bucket): time every candidate engine (CUDA cores, TF32 / BF16 tensor cores, FP8 E4M3 for
+    BF16 inputs) with time_fn(n, k, dtype, engine) -> ms per block (None when the engine cannot run the shape) and
+    keep the fastest. Results are cached in memory and, with
     cache_path, in a JSON file reused by later runs."""
 
-    def __init__(self, time_fn, candidates=(S.SMP_ENGINE_SIMT, S.SMP_ENGINE_TC), cache_path=None):
+    def __init__(self, time_fn, candidates=(S.SMP_ENGINE_SIMT, S.SMP_ENGINE_TC, S.SMP_ENGINE_TC_FP8),
+                 cache_path=None):
         self.time_fn, self.candidates, self.cache_path = time_fn, tuple(candidates), cache_path
         self.cache = {}
         self.trials = 0

@@ -241,3 +241,29 @@ def test_exact_entries_at_the_scale_shape(env):
     assert np.all(np.abs(vals[pick] - want) <= (2.0 ** -10 + R * 2.0 ** -23) * scale)
     assert np.linalg.norm(vals[pick] - want) <= 1e-3 * np.linalg.norm(want)
     s.close()
+
+
+def test_table1_error_evaluator_matches_dense(env):
+    """bench.py's implicit spectral-error evaluator (used where A^T A is too large to form) against dense SVDs of
+    A^T A on a G D instance small enough to form (d = n = 1,500), with LELA's factors and a random rank-5 pair."""
+    torch, smp, pipeline = env
+    import bench
+    from paper_1610_06656_gb300 import synth as sy
+    n, r = 1500, 5
+    A = sy.gd_torch(n, n, seed=3, device="cuda")
+    s = pipeline.Solver(n, n, 16, torch.float32, seed=1, same_ab=True, max_rows=1024)
+    out = s.lela(A, None, r, 10, block_rows=1024)
+    s.close()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    rnd = (torch.randn(n, r, generator=g, device="cuda", dtype=torch.float64),
+           torch.rand(r, generator=g, device="cuda", dtype=torch.float64),
+           torch.randn(n, r, generator=g, device="cuda", dtype=torch.float64))
+    factors = [(out["U"], out["S"], out["V"]), rnd]
+    errs, opt = bench.implicit_errors(torch, A, factors, r)
+    M = A.double().T @ A.double()
+    sv = torch.linalg.svdvals(M)
+    assert abs(opt - float(sv[r] / sv[0])) <= 1e-4 * float(sv[r] / sv[0])
+    for (U, S, V), e in zip(factors, errs):
+        want = float(torch.linalg.matrix_norm(M - (U * S) @ V.T, ord=2) / sv[0])
+        assert abs(e - want) <= 1e-3 * want

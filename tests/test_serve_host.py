@@ -65,10 +65,12 @@ def test_batch_instances_and_tuner_cache(tmp_path):
     assert len(specs) == 256 and all(s.arrival == 0.0 and s.k == 8 * s.r for s in specs)
     calls = []
 
-    def fake(n, k, dtype, engine):          # the tensor-core engine wins from n = 512 up; SIMT cannot run k = 160
-        calls.append((n, k, engine))
+    def fake(n, k, dtype, engine):          # the tensor-core engine wins from n = 512 up; SIMT cannot run k = 160;
+        calls.append((n, k, engine))        # FP8 takes BF16 inputs only and wins on them from n = 1,024 up
         if engine == S.SMP_ENGINE_SIMT:
             return None if k == 160 else 1.0
+        if engine == S.SMP_ENGINE_TC_FP8:
+            return None if dtype != S.SMP_BF16 else (0.3 if n >= 1024 else 3.0)
         return 0.5 if n >= 512 else 2.0
 
     path = str(tmp_path / "tune.json")
@@ -77,7 +79,9 @@ def test_batch_instances_and_tuner_cache(tmp_path):
     assert t.choose(120, 40, S.SMP_F32) == S.SMP_ENGINE_SIMT            # same bucket (128): cached
     assert t.choose(1000, 40, S.SMP_F32) == S.SMP_ENGINE_TC
     assert t.choose(100, 160, S.SMP_F32) == S.SMP_ENGINE_TC             # SIMT unavailable
-    assert t.trials == 6 and len(calls) == 6
+    assert t.trials == 9 and len(calls) == 9                            # three candidates per shape key
+    assert t.choose(1000, 40, S.SMP_BF16) == S.SMP_ENGINE_TC_FP8
+    assert t.choose(200, 40, S.SMP_BF16) == S.SMP_ENGINE_SIMT           # bucket 256: FP8 and TF32 slower
     t2 = batch.EngineTuner(fake, cache_path=path)                       # reloaded from the file: no new trials
     assert t2.choose(1000, 40, S.SMP_F32) == S.SMP_ENGINE_TC and t2.trials == 0
     assert batch.n_bucket(64) == 64 and batch.n_bucket(65) == 128 and batch.n_bucket(2048) == 2048
