@@ -200,7 +200,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="scale", choices=sorted(WORKLOADS))
-    ap.add_argument("--engine", default="auto", choices=["auto", "simt", "tc", "srht"])
+    ap.add_argument("--engine", default="auto", choices=["auto", "simt", "tc", "tc_bf16", "srht"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-error", action="store_true")
@@ -234,7 +234,7 @@ def main():
     if world > 1:
         dist.barrier()
     engine = {"auto": smp.SMP_ENGINE_AUTO, "simt": smp.SMP_ENGINE_SIMT, "tc": smp.SMP_ENGINE_TC,
-              "srht": smp.SMP_ENGINE_SRHT}[args.engine]
+              "tc_bf16": smp.SMP_ENGINE_TC_BF16, "srht": smp.SMP_ENGINE_SRHT}[args.engine]
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     A, B, _, _, _ = synth.lowrank_plus_noise_torch(w["d"], w["n1"], w["n2"], w["L"], w["sigma"], w["alpha"],
@@ -326,11 +326,15 @@ def main():
     sk_bytes = sum(sk_rows) * ntot * 4 / len(sk_rows)          # algorithmic bytes per launch: A and B rows read once
     sk_flops = 2.0 * w["k"] * sum(sk_rows) * ntot / len(sk_rows)
     sk_avg_s = sum(sk_ms) / len(sk_ms) / 1e3
-    tc_used = engine == smp.SMP_ENGINE_TC or (engine == smp.SMP_ENGINE_AUTO and tc_active(smp))
+    b16ops = engine == smp.SMP_ENGINE_TC_BF16
+    tc_used = engine in (smp.SMP_ENGINE_TC, smp.SMP_ENGINE_TC_BF16) or (engine == smp.SMP_ENGINE_AUTO and tc_active(smp))
     srht = engine == smp.SMP_ENGINE_SRHT
     if srht:
         roof = {"bound": "hbm", "achieved": sk_bytes / sk_avg_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "peak_kind": "%s HBM copy" % peak_kind}
+    elif b16ops:
+        roof = {"bound": "tensor", "achieved": sk_flops / sk_avg_s / 1e12, "peak": peaks["bf16_tflops"],
+                "unit": "TFLOP/s", "peak_kind": "%s bf16 burst" % peak_kind}
     elif tc_used:
         tf32_peak = peaks["bf16_tflops"] * (1.1 / 2.25)
         roof = {"bound": "tensor", "achieved": sk_flops / sk_avg_s / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
@@ -341,8 +345,10 @@ def main():
         roof = {"bound": "alu", "achieved": sk_flops / sk_avg_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
                 "peak_kind": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x %.0f MHz" % clk_mhz}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = sketch_traffic(sum(sk_rows) / len(sk_rows)) if tc_used else None
+    roof["traffic"] = sketch_traffic(sum(sk_rows) / len(sk_rows)) if tc_used and not b16ops else None
     roof["kernel"] = ("smp_sketch_accumulate: block SRHT (srht_fused_kernel)" if srht else
+                      "smp_sketch_accumulate: sketch_tc_kernel<BF16 operands> (tcgen05 kind::f16), Pi of the next "
+                      "block generated on a side stream meanwhile" if b16ops else
                       "smp_sketch_accumulate: sketch_tc_kernel (tcgen05), Pi of the next block generated on a side "
                       "stream meanwhile" if tc_used else "sketch_simt_kernel")
     roof["hbm_gbs"] = sk_bytes / sk_avg_s / 1e9
@@ -462,7 +468,8 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "tf32" if tc_used else "f32",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16 operands (f32 inputs)" if b16ops else ("tf32" if tc_used else "f32"),
                 "data": "synthetic (low rank 20 + noise 0.1, column scales (j+1)^-0.5, torch RNG seeded per rank)",
                 "config": {"workload": args.workload, **{k: w[k] for k in ("d", "n1", "n2", "k", "r", "T")},
                            "block_rows": w["block"], "m": m, "nnz": int(nnz), "parallelism": "replicas",

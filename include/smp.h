@@ -68,7 +68,7 @@ typedef enum {
                               one power of two per matrix, 2^ceil(log2(max |x| / 448)), Pi is E4M3 of the normals,
                               FP32 accumulation; column norms of the stored BF16 values. k <= 1024, alignment as for
                               SMP_BF16. Never chosen by SMP_ENGINE_AUTO. */
-    SMP_ENGINE_SRHT = 4    /* block SRHT as Pi (Section 4: the Spark implementation's sketch) instead of the Gaussian:
+    SMP_ENGINE_SRHT = 4,   /* block SRHT as Pi (Section 4: the Spark implementation's sketch) instead of the Gaussian:
                               data rows in blocks of R = max_rows rows (a power of two in [256, 2^16]; block b =
                               rows [bR, (b+1)R)), Pi_b = k^-1/2 S_b H_R D_b with D_b the signs of Philox counter
                               (t mod 2^32, t >> 32, 0, 6) (bit 0 of word 0 set: -1), H_R the unnormalised Sylvester
@@ -76,6 +76,11 @@ typedef enum {
                               log2(R) bits of word 0 of counter (a, b mod 2^32, b >> 32, 7)). SMP_F32 only; every
                               accumulate call covers one block (row0 % max_rows == 0); binary32 arithmetic, norms
                               compensated as in the other engines. Never chosen by SMP_ENGINE_AUTO. */
+    SMP_ENGINE_TC_BF16 = 5 /* tcgen05 sketch of SMP_F32 row blocks with BF16 operands: the kernel rounds each input
+                              to BF16 (nearest, ties to even) on its way to the tensor cores, Pi is generated in
+                              BF16, accumulation in FP32 (kind::f16), column norms compensated from the binary32
+                              inputs; k <= 512, alignment as SMP_ENGINE_TC's SMP_F32 case. Never chosen by
+                              SMP_ENGINE_AUTO. */
 } smp_engine;
 
 /* smp_waltmin flags */

@@ -165,7 +165,9 @@ smp_status smp_sketch_begin(const smp_params* params, void* stream, smp_ctx** ou
         return fail(nullptr, SMP_EINVAL, "n1, n2 must be in [1, 2^30]");
     if (p.same_ab && p.n1 != p.n2) return fail(nullptr, SMP_EINVAL, "same_ab needs n1 == n2");
     if (p.k < 1 || p.k > 4096) return fail(nullptr, SMP_EINVAL, "k must be in [1, 4096]");
-    if (p.engine < SMP_ENGINE_AUTO || p.engine > SMP_ENGINE_SRHT) return fail(nullptr, SMP_EINVAL, "unknown engine");
+    if (p.engine < SMP_ENGINE_AUTO || p.engine > SMP_ENGINE_TC_BF16) return fail(nullptr, SMP_EINVAL, "unknown engine");
+    if (p.engine == SMP_ENGINE_TC_BF16 && p.dtype != SMP_F32)
+        return fail(nullptr, SMP_EUNSUPPORTED, "SMP_ENGINE_TC_BF16 takes SMP_F32 row blocks");
     if (p.engine == SMP_ENGINE_SRHT) {
         if (p.dtype != SMP_F32) return fail(nullptr, SMP_EUNSUPPORTED, "SMP_ENGINE_SRHT takes SMP_F32 row blocks");
         const int64_t R = p.max_rows ? p.max_rows : 65536;
@@ -250,11 +252,12 @@ smp_status smp_sketch_accumulate(smp_ctx* c, const void* A, int64_t lda, const v
     }
     const bool bf16 = c->p.dtype == SMP_BF16;
     const bool tc_ok = bf16 ? bf16_block_ok(c, A, lda, B, ldb) : tc_block_ok(c, A, lda, B, ldb);
-    if (c->p.engine == SMP_ENGINE_TC && !tc_ok)
+    const bool tc_engine = c->p.engine == SMP_ENGINE_TC || c->p.engine == SMP_ENGINE_TC_BF16;
+    if (tc_engine && !tc_ok)
         return fail(c, SMP_EUNSUPPORTED,
                     "the tensor-core sketch needs SMP_F32 with k <= 512 and lda, ldb % 4 == 0, or SMP_BF16 with "
                     "k <= 1024 and lda, ldb % 8 == 0, and 16-byte aligned blocks");
-    const bool want_tc = c->p.engine == SMP_ENGINE_TC || (c->p.engine == SMP_ENGINE_AUTO && tc_ok);
+    const bool want_tc = tc_engine || (c->p.engine == SMP_ENGINE_AUTO && tc_ok);
     if ((s = track_rows(c, row0, nrows)) != SMP_OK) return s;
     cudaError_t e = !want_tc ? launch_sketch_simt(c, A, lda, B, ldb, row0, nrows, nullptr, 0)
                              : bf16 ? launch_sketch_bf16(c, A, lda, B, ldb, row0, nrows, nullptr, 0)
@@ -280,10 +283,11 @@ smp_status smp_sketch_accumulate_pi(smp_ctx* c, const void* Pi, int64_t ldp, con
     const bool bf16 = c->p.dtype == SMP_BF16;
     const bool tc_ok = bf16 ? bf16_block_ok(c, A, lda, B, ldb)
                             : tc_block_ok(c, A, lda, B, ldb) && ((uintptr_t)Pi % 16 == 0) && (ldp % 4 == 0);
-    if (c->p.engine == SMP_ENGINE_TC && !tc_ok)
+    const bool tc_engine = c->p.engine == SMP_ENGINE_TC || c->p.engine == SMP_ENGINE_TC_BF16;
+    if (tc_engine && !tc_ok)
         return fail(c, SMP_EUNSUPPORTED, "the tensor-core sketch needs 16-byte aligned Pi and ldp % 4 == 0");
     if ((s = track_rows(c, row0, nrows)) != SMP_OK) return s;
-    if (c->p.engine == SMP_ENGINE_TC || (c->p.engine == SMP_ENGINE_AUTO && tc_ok))
+    if (tc_engine || (c->p.engine == SMP_ENGINE_AUTO && tc_ok))
         return check_cuda(c,
                           bf16 ? launch_sketch_bf16(c, A, lda, B, ldb, row0, nrows, (const float*)Pi, ldp)
                                : launch_sketch_tc_pi(c, A, lda, B, ldb, row0, nrows, (const float*)Pi, ldp),

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <mutex>
 
@@ -58,6 +59,17 @@ constexpr int DATA_STAGE_BYTES = 4 * KS * 32 * 4;           // 128 columns x KS 
 constexpr int KGROUP_BYTES = 4 * DATA_BOX_BYTES;            // one 8-row group of all four boxes
 constexpr int A_STAGE_BYTES = TILE_M * KS * 4;             // K-major copy: 128 rows x 64 B (64-byte swizzle)
 constexpr int PI_BOX_BYTES = PI_BOX_ROWS * KS * 4;          // 256 rows x KS fp32
+// The two operand variants: TF32 (16 data rows per stage, two K = 8 slices per MMA pass) and BF16 operands of
+// binary32 inputs (32 rows per stage, two K = 16 slices). Both give 64-byte K-major operand rows (64-byte swizzle,
+// 8-row groups 512 B apart, 32-byte K slices), the same copy and Pi stage sizes and the same data ring in bytes.
+template <bool B16>
+struct Geo {
+    static constexpr int KS = B16 ? 32 : 16;
+    static constexpr int DSTAGES = B16 ? SMP_TC_DSTAGES / 2 : SMP_TC_DSTAGES;
+    static constexpr int DATA_STAGE_BYTES = 4 * KS * 32 * 4;
+};
+static_assert(Geo<true>::DSTAGES * Geo<true>::DATA_STAGE_BYTES == DSTAGES * DATA_STAGE_BYTES, "same data ring");
+static_assert(TILE_M * 32 * 2 == A_STAGE_BYTES && PI_BOX_ROWS * 32 * 2 == PI_BOX_BYTES, "same operand stages");
 constexpr int PI_STAGE_BYTES = (MAX_KC / PI_BOX_ROWS) * PI_BOX_BYTES;
 constexpr int DRING_BYTES = DSTAGES * DATA_STAGE_BYTES;
 constexpr int ARING_BYTES = ASTAGES * A_STAGE_BYTES;
@@ -89,6 +101,17 @@ __device__ __forceinline__ float to_tf32(float x) {
     uint32_t y;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
     return __uint_as_float(y);
+}
+
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+    uint32_t y;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+    return y;
+}
+// Two values rounded to BF16 (nearest, ties to even), the first in the low half (the lower K index).
+__device__ __forceinline__ uint32_t bf16_pair(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
 }
 
 __device__ __forceinline__ void store_pi(float* p, float z) { *p = to_tf32(z); }
@@ -133,10 +156,14 @@ struct TcArgs {
     int* err;
 };
 
+template <bool B16>
 __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_constant__ CUtensorMap tm_a,
                                                                const __grid_constant__ CUtensorMap tm_b,
                                                                const __grid_constant__ CUtensorMap tm_pi,
                                                                const TcArgs args) {
+    constexpr int KS = Geo<B16>::KS;
+    constexpr int DSTAGES = Geo<B16>::DSTAGES;
+    constexpr int DATA_STAGE_BYTES = Geo<B16>::DATA_STAGE_BYTES;
     extern __shared__ uint8_t smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int split = blockIdx.y;
@@ -265,8 +292,8 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer (the whole warp waits; lane 0 issues)
-        const uint32_t id_full = idesc_tf32(TILE_M, PI_BOX_ROWS);
-        const uint32_t id_last = idesc_tf32(TILE_M, args.n_last);
+        const uint32_t id_full = B16 ? idesc_bf16(TILE_M, PI_BOX_ROWS, false) : idesc_tf32(TILE_M, PI_BOX_ROWS);
+        const uint32_t id_last = B16 ? idesc_bf16(TILE_M, args.n_last, false) : idesc_tf32(TILE_M, args.n_last);
         bool ok = true;
         for (int it = 0; it < n_it; ++it) {
             const int sp = it % PSTAGES, sa = it % ASTAGES;
@@ -284,13 +311,18 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
             if (lane == 0) {
                 const uint32_t abase = aring + sa * A_STAGE_BYTES, pbase = pring + sp * PI_STAGE_BYTES;
 #pragma unroll
-                for (int kb = 0; kb < KS / 8; ++kb) {
-                    // both operands K-major, 64B swizzle: rows of 64 B, 8-row groups 512 B apart (SBO), K slice at +32 B
+                for (int kb = 0; kb < 2; ++kb) {
+                    // both operands K-major, 64B swizzle: rows of 64 B, 8-row groups 512 B apart (SBO), K slice
+                    // (8 TF32 or 16 BF16 values) at +32 B
                     const uint64_t ad = smem_desc(abase + kb * 32, 16, 512, SWZ_64B);
                     for (int h = 0; h < args.nh; ++h) {
                         const uint64_t bd = smem_desc(pbase + h * PI_BOX_BYTES + kb * 32, 16, 512, SWZ_64B);
-                        mma_tf32(tmem + h * PI_BOX_ROWS, ad, bd, h == args.nh - 1 ? id_last : id_full,
-                                 (it > 0 || kb > 0) ? 1u : 0u);
+                        if (B16)
+                            mma_bf16(tmem + h * PI_BOX_ROWS, ad, bd, h == args.nh - 1 ? id_last : id_full,
+                                     (it > 0 || kb > 0) ? 1u : 0u);
+                        else
+                            mma_tf32(tmem + h * PI_BOX_ROWS, ad, bd, h == args.nh - 1 ? id_last : id_full,
+                                     (it > 0 || kb > 0) ? 1u : 0u);
                     }
                 }
                 mma_commit(aempty_bar(sa));
@@ -301,11 +333,12 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
         if (ok && lane == 0) mma_commit(acc_bar);
         __syncwarp();
     } else if (copy_index(warp) >= 0) {
-        // ---------------- copy warps: one (32-column box, 8-row group) each: column sums of squares + K-major TF32
-        // copy of their 8 rows
+        // ---------------- copy warps: a 32-column box and the 8-row groups ci / 4 (+ 2) of the stage: column sums of
+        // squares and the K-major operand copy of their rows (TF32: 16 B per 4 rows; BF16: 16 B per 8 rows)
         const int ci = copy_index(warp);
-        const int box = ci & 3, grp = ci >> 2;
+        const int box = ci & 3, grp0 = ci >> 2;
         const int m = box * 32 + lane;   // data column within the tile
+        constexpr int NG = KS / 16;      // 8-row groups per copy warp
         for (int it = 0; it < n_it; ++it) {
             const int d = it % DSTAGES;
             const uint32_t dph = (uint32_t)(it / DSTAGES) & 1u;
@@ -322,20 +355,39 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
                 break;
             }
             // staged box: 128B swizzle, the 16-byte chunk q of row t sits at chunk q ^ (t & 7)
-            const float* box_p =
-                (const float*)(base_ptr + d * DATA_STAGE_BYTES + grp * KGROUP_BYTES + box * DATA_BOX_BYTES);
-            float x[8];
+            float x[NG][8];
 #pragma unroll
-            for (int t = 0; t < 8; ++t) x[t] = box_p[t * 32 + (((lane >> 2) ^ t) << 2) + (lane & 3)];
+            for (int g = 0; g < NG; ++g) {
+                const float* box_p = (const float*)(base_ptr + d * DATA_STAGE_BYTES + (grp0 + 2 * g) * KGROUP_BYTES +
+                                                    box * DATA_BOX_BYTES);
+#pragma unroll
+                for (int t = 0; t < 8; ++t) x[g][t] = box_p[t * 32 + (((lane >> 2) ^ t) << 2) + (lane & 3)];
+            }
             __syncwarp();
             if (lane == 0) mbar_arrive(dempty_bar(d));   // staging read: the producer may refill it
+            // K-major copy: data column m is row m (64 B); the 64B swizzle puts chunk q at q ^ ((m >> 1) & 3)
+            uint4* arow = (uint4*)(base_ptr + DRING_BYTES + s * A_STAGE_BYTES + m * 64);
+            const int sw = (m >> 1) & 3;
 #pragma unroll
-            for (int t = 0; t < 8; t += 2) two_sum_square_x2(pack2(x[t], x[t + 1]), hi2, lo2);
-            // K-major copy: data column m is row m (64 B = KS values); 64B swizzle puts chunk q at q ^ ((m >> 1) & 3)
-            float4* arow = (float4*)(base_ptr + DRING_BYTES + s * A_STAGE_BYTES + m * (KS * 4));
-            const int q0 = 2 * grp;
-            arow[q0 ^ ((m >> 1) & 3)] = make_float4(to_tf32(x[0]), to_tf32(x[1]), to_tf32(x[2]), to_tf32(x[3]));
-            arow[(q0 + 1) ^ ((m >> 1) & 3)] = make_float4(to_tf32(x[4]), to_tf32(x[5]), to_tf32(x[6]), to_tf32(x[7]));
+            for (int g = 0; g < NG; ++g) {
+#pragma unroll
+                for (int t = 0; t < 8; t += 2) two_sum_square_x2(pack2(x[g][t], x[g][t + 1]), hi2, lo2);
+                if (B16) {   // rows 8 gg .. 8 gg + 7 as BF16 (round to nearest even) in chunk gg
+                    const int gg = grp0 + 2 * g;
+                    uint4 v;
+                    v.x = bf16_pair(x[g][0], x[g][1]);
+                    v.y = bf16_pair(x[g][2], x[g][3]);
+                    v.z = bf16_pair(x[g][4], x[g][5]);
+                    v.w = bf16_pair(x[g][6], x[g][7]);
+                    arow[gg ^ sw] = v;
+                } else {     // rows 8 grp0 .. 8 grp0 + 7 as TF32 in chunks 2 grp0, 2 grp0 + 1
+                    const int q0 = 2 * grp0;
+                    arow[q0 ^ sw] = make_uint4(tf32_bits(x[g][0]), tf32_bits(x[g][1]), tf32_bits(x[g][2]),
+                                               tf32_bits(x[g][3]));
+                    arow[(q0 + 1) ^ sw] = make_uint4(tf32_bits(x[g][4]), tf32_bits(x[g][5]), tf32_bits(x[g][6]),
+                                                     tf32_bits(x[g][7]));
+                }
+            }
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(afull_bar(s));
@@ -471,7 +523,8 @@ PiGeom pi_geom(const smp_ctx* c) {
     PiGeom g;
     g.kpad = (int)round_up(round_up(c->p.k, 16), 256);
     g.ld = round_up(c->max_rows, PI_ROW_PAD);
-    g.esize = c->p.engine == SMP_ENGINE_TC_FP8 ? 1 : (c->p.dtype == SMP_BF16 ? 2 : 4);
+    g.esize = c->p.engine == SMP_ENGINE_TC_FP8 ? 1
+              : (c->p.dtype == SMP_BF16 || c->p.engine == SMP_ENGINE_TC_BF16) ? 2 : 4;
     return g;
 }
 
@@ -573,42 +626,52 @@ bool tc_block_ok(const smp_ctx* c, const void* A, int64_t lda, const void* B, in
 
 cudaError_t launch_sketch_tc_pi(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t row0,
                                 int64_t nrows, const float* Pi, int64_t ldp) {
-    static std::atomic<bool> attr{false};
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    // SMP_ENGINE_TC_BF16: BF16 operands (32 rows per stage, Pi in BF16); otherwise TF32 operands
+    const bool b16 = c->p.engine == SMP_ENGINE_TC_BF16;
+    static std::atomic<bool> attr[2] = {{false}, {false}};
+    if (!attr[b16]) {
+        cudaError_t e = cudaFuncSetAttribute(b16 ? sketch_tc_kernel<true> : sketch_tc_kernel<false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr[b16] = true;
     }
+    const int ks = b16 ? Geo<true>::KS : Geo<false>::KS;
     const int k = c->p.k;
     const int kc = (int)round_up(k, 32);                 // TMEM columns drained (multiple of 32)
     const int kmma = (int)round_up(k, 16);               // MMA N coverage
     const int nh = (kmma + PI_BOX_ROWS - 1) / PI_BOX_ROWS;
     const int n_last = kmma - (nh - 1) * PI_BOX_ROWS;
-    const int64_t tpad = round_up(nrows, KS);
+    const int64_t tpad = round_up(nrows, ks);
     cudaStream_t st = c->stream;
-    const float* pi = Pi;
+    const void* pi = Pi;
     int64_t pld = ldp;
     int64_t pi_rows = k;
+    int64_t pi_inner = nrows;
     int buf = -1;
-    if (!pi) {
-        // generated Pi: kpad rows (zero beyond k), double-buffered and generated one block ahead on a side stream
-        cudaError_t e = pi_acquire(c, row0, nrows, &buf);
+    if (!pi || b16) {
+        // generated Pi (kpad rows, zero beyond k; double-buffered, generated one block ahead on a side stream), or
+        // the caller's Pi rounded to BF16 into a Pi buffer
+        cudaError_t e = pi ? pi_import(c, Pi, ldp, nrows, &buf) : pi_acquire(c, row0, nrows, &buf);
         if (e != cudaSuccess) return e;
         const PiGeom gm = pi_geom(c);
-        pi = (const float*)c->pi_buf[buf];
+        pi = c->pi_buf[buf];
         pld = gm.ld;
         pi_rows = gm.kpad;
+        pi_inner = tpad;
     }
     CUtensorMap ma, mb, mp;
     const void* Bp = c->p.same_ab ? A : B;
     const int64_t n2 = c->p.same_ab ? 0 : c->p.n2;
-    // data boxes: 32 columns (128 B, one swizzle row) x 8 rows = DATA_BOX_BYTES, matching the kernel's expect_tx
+    // data boxes: 32 columns (128 B, one swizzle row) x 8 rows = DATA_BOX_BYTES, matching the kernel's expect_tx;
+    // Pi boxes: 64-byte rows (16 TF32 or 32 BF16 values) x 256 sketch rows
     if (!make_map(&ma, A, (uint64_t)c->p.n1, (uint64_t)nrows, (uint64_t)lda, 32, DATA_BOX_ROWS, CU_TENSOR_MAP_SWIZZLE_128B) ||
         !make_map(&mb, Bp, (uint64_t)(c->p.same_ab ? c->p.n1 : c->p.n2), (uint64_t)nrows,
                   (uint64_t)(c->p.same_ab ? lda : ldb), 32, DATA_BOX_ROWS,
                   CU_TENSOR_MAP_SWIZZLE_128B) ||
-        !make_map(&mp, pi, (uint64_t)(Pi ? nrows : tpad), (uint64_t)pi_rows, (uint64_t)pld, KS, PI_BOX_ROWS,
-                  CU_TENSOR_MAP_SWIZZLE_64B))
+        !(b16 ? make_map(&mp, pi, (uint64_t)pi_inner, (uint64_t)pi_rows, (uint64_t)pld, ks, PI_BOX_ROWS,
+                         CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2)
+              : make_map(&mp, pi, (uint64_t)pi_inner, (uint64_t)pi_rows, (uint64_t)pld, ks, PI_BOX_ROWS,
+                         CU_TENSOR_MAP_SWIZZLE_64B)))
         return cudaErrorInvalidValue;
     TcArgs a;
     a.n1 = c->p.n1;
@@ -624,17 +687,23 @@ cudaError_t launch_sketch_tc_pi(smp_ctx* c, const void* A, int64_t lda, const vo
     while ((int)cols < kc) cols <<= 1;
     a.tmem_cols = cols;
     a.nrows = nrows;
-    const int64_t steps = tpad / KS;
+    const int64_t steps = tpad / ks;
     int splits = std::max(1, std::min(c->splits, c->sm_count / std::max(1, tiles)));
     splits = (int)std::min<int64_t>(splits, steps);
-    a.rows_per_split = ((steps + splits - 1) / splits) * KS;
+    a.rows_per_split = ((steps + splits - 1) / splits) * ks;
     a.ldk = c->ldk;
     a.part = (float*)c->part;
     a.nsq = c->nsq;
     a.err = c->dev_err;
-    sketch_tc_kernel<<<smp::counted(dim3((unsigned)tiles, (unsigned)splits)), THREADS, SMEM_BYTES, st>>>(ma, mb, mp, a);
+    const dim3 grid = smp::counted(dim3((unsigned)tiles, (unsigned)splits));
+    if (b16) sketch_tc_kernel<true><<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, mp, a);
+    else sketch_tc_kernel<false><<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, mp, a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || buf < 0) return e;
+    if (Pi) {   // a caller's Pi: the buffer only becomes free again, nothing is generated ahead
+        c->pi_last = buf;
+        return cudaEventRecord(c->pi_free[buf], st);
+    }
     // the sketch reads buffer `buf` until it ends; meanwhile the other buffer gets Pi of the next row block
     return pi_release(c, buf, row0, nrows);
 }

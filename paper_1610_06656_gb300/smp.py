@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(PKG, "libsmp.so")
 
 SMP_OK, SMP_EINVAL, SMP_ENOMEM, SMP_ECUDA, SMP_ESTATE, SMP_ETIMEOUT, SMP_ENUMERIC, SMP_EUNSUPPORTED, SMP_EBUSY = range(9)
 SMP_F32, SMP_BF16, SMP_F64 = 0, 1, 2
-SMP_ENGINE_AUTO, SMP_ENGINE_SIMT, SMP_ENGINE_TC, SMP_ENGINE_TC_FP8, SMP_ENGINE_SRHT = 0, 1, 2, 3, 4
+SMP_ENGINE_AUTO, SMP_ENGINE_SIMT, SMP_ENGINE_TC, SMP_ENGINE_TC_FP8, SMP_ENGINE_SRHT, SMP_ENGINE_TC_BF16 = 0, 1, 2, 3, 4, 5
 SMP_SPLIT_OMEGA, SMP_NO_TRIM, SMP_INIT_GIVEN, SMP_FP64_ALS = 1, 2, 4, 8
 
 _c = ctypes
