@@ -248,8 +248,8 @@ def main():
     solver = solvers[0]
     m = pipeline.default_m(w["n1"], w["n2"], w["r"])
 
-    def sketch_timed(i, evs):
-        sv, st = solvers[i % 2], streams[i % 2]
+    def sketch_timed(i, evs, svs, sts):
+        sv, st = svs[i % 2], sts[i % 2]
         smp.smp_sketch_reset(sv.ctx)
         for r0 in range(0, w["d"], w["block"]):
             r1 = min(w["d"], r0 + w["block"])
@@ -261,20 +261,20 @@ def main():
             evs.append((e0, e1, r1 - r0))
         smp.smp_sketch_finalize(sv.ctx)
 
-    def run_steps(count, evs, step_events):
+    def run_steps(count, evs, step_events, svs=solvers, sts=streams):
         """count solves, pipelined: solve i's sketch was issued before solve i - 1's WAltMin."""
         out = None
         marks = {}
 
         def issue(i):
             s0 = torch.cuda.Event(enable_timing=True)
-            s0.record(streams[i % 2])
+            s0.record(sts[i % 2])
             marks[i] = s0
-            sketch_timed(i, evs)
+            sketch_timed(i, evs, svs, sts)
 
         issue(0)
         for i in range(count):
-            sv, st = solvers[i % 2], streams[i % 2]
+            sv, st = svs[i % 2], sts[i % 2]
             nnz = sv.sample(m, 2 + rank)
             with torch.cuda.stream(st):
                 vals = sv.estimate(nnz)
@@ -355,6 +355,39 @@ def main():
     roof["hbm_frac"] = roof["hbm_gbs"] / peaks["hbm_gbs"]
     roof["launch_ms"] = sk_avg_s * 1e3
     roof["bytes_per_launch"] = sk_bytes
+
+    # the same pipelined solves with BF16 tensor-core operands for the binary32 inputs (SMP_ENGINE_TC_BF16), outside
+    # the timed region above: solves/s, sketch rate against the BF16 peak, and (below) the spectral error
+    alt = None
+    if rank == 0 and not args.no_baseline and tc_used and not b16ops and not srht:
+        a_streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+        a_solvers = [pipeline.Solver(w["n1"], w["n2"], w["k"], torch.float32, seed=1 + rank,
+                                     engine=smp.SMP_ENGINE_TC_BF16, max_rows=w["block"], stream=st.cuda_stream)
+                     for st in a_streams]
+        run_steps(args.warmup, [], [], a_solvers, a_streams)
+        torch.cuda.synchronize()
+        a_sk, a_steps = [], []
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for st in a_streams:
+            st.wait_event(a0)
+        (Ua, Sa, Va), _ = run_steps(args.steps, a_sk, a_steps, a_solvers, a_streams)
+        for st in a_streams:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            stream.wait_event(ev)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        a_launch = sum(x.elapsed_time(y) for x, y, _ in a_sk) / len(a_sk) / 1e3
+        alt = {"name": "SMP_ENGINE_TC_BF16: the same inputs with BF16 tensor-core operands "
+                       "(sketch_tc_kernel<BF16 operands>, kind::f16)",
+               "solves_per_s": args.steps / (a0.elapsed_time(a1) / 1e3),
+               "p50_ms": statistics.median(sorted(x.elapsed_time(y) for x, y in a_steps)),
+               "sketch_launch_ms": a_launch * 1e3, "sketch_tflops": sk_flops / a_launch / 1e12,
+               "sketch_frac_of_bf16_peak": sk_flops / a_launch / 1e12 / peaks["bf16_tflops"],
+               "sketch_hbm_frac": sk_bytes / a_launch / 1e9 / peaks["hbm_gbs"], "spectral_err": None}
+        for sv in a_solvers:
+            sv.close()
 
     # the paper's comparison, SVD(A~^T B~) by power iteration on the last step's sketches (outside the timed
     # region; smp_sketch_svd synchronises, so host wall time is its duration)
@@ -439,15 +472,14 @@ def main():
 
     err, opt_err = None, None
     if not args.no_error and rank == 0:
-        extra = ([(Ub, Sb, Vb)] if base else []) + ([(Um, Sm, Vm)] if mn else []) + ([(Ul, Sl, Vl)] if lela else [])
+        extra = ([(Ub, Sb, Vb)] if base else []) + ([(Um, Sm, Vm)] if mn else []) + ([(Ul, Sl, Vl)] if lela else []) \
+            + ([(Ua, Sa, Va)] if alt else [])
         errs, opt_err = spectral_error(torch, A, B, [(U, S, V)] + extra)
         err = errs[0]
-        if base:
-            base["spectral_err"] = errs[1]
-        if mn:
-            mn["spectral_err"] = errs[1 + (1 if base else 0)]
-        if lela:
-            lela["spectral_err"] = errs[-1]
+        rest = errs[1:]
+        for entry in (base, mn, lela, alt):
+            if entry:
+                entry["spectral_err"] = rest.pop(0)
 
     # ---- end to end: host-resident inputs copied in every step (pinned, double-buffered row blocks)
     e2e = None
@@ -478,7 +510,7 @@ def main():
                 "p50_ms": statistics.median(step_ms), "p99_ms": step_ms[min(len(step_ms) - 1,
                                                                             int(math.ceil(0.99 * len(step_ms))) - 1)],
                 "sketch_gbs": roof["hbm_gbs"], "spectral_err": err, "optimal_err": opt_err,
-                "baseline_sketch_svd": base, "sampler_multinomial": mn, "lela": lela,
+                "baseline_sketch_svd": base, "sampler_multinomial": mn, "lela": lela, "engine_bf16_operands": alt,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk}
         print(json.dumps(line), flush=True)
