@@ -22,6 +22,40 @@ namespace smp {
 std::atomic<uint64_t> g_launches{0};
 std::atomic<int32_t> g_fail_allocs{0};
 
+cudaStream_t release_stream() {
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        streams[dev] = nullptr;
+    }
+    return streams[dev];
+}
+
+void free_idle(void* p) {
+    if (p) cudaFreeAsync(p, release_stream());
+}
+
+void release_after(cudaStream_t st) {
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+        if (cudaEventRecord(ev, st) != cudaSuccess || cudaStreamWaitEvent(release_stream(), ev, 0) != cudaSuccess)
+            cudaStreamSynchronize(st);   // cannot order the release stream: wait for st instead
+        cudaEventDestroy(ev);
+    } else {
+        cudaStreamSynchronize(st);
+    }
+}
+
+void free_after(void* p, cudaStream_t st) {
+    if (!p) return;
+    release_after(st);
+    free_idle(p);
+}
+
 smp_status fail(smp_ctx* c, smp_status s, const std::string& msg) {
     if (c) c->err = msg;
     else g_begin_error = msg;
@@ -61,9 +95,10 @@ void free_ctx(smp_ctx* c) {
                     c->col,    c->qhat,   c->csc_row, c->csc_pos, c->alpha,   c->beta,  c->mask,    c->wpre,
                     c->erow,   c->srht_y, c->srht_nsq, c->srht_rows, c->mn_S,   c->mn_bcum, c->mn_btot, c->mn_rows, c->mn_off, c->mn_draw, c->mn_count,
                     c->row_cnt, c->col_cnt, c->ex_part, c->ex_at, c->dev_err};
-    // stream-ordered frees: no device-wide synchronisation, so other contexts' work keeps running
-    for (void* p : ptrs)
-        if (p) cudaFreeAsync(p, c->stream);
+    // stream-ordered frees behind the context's queued work, on the shared release stream: no device-wide
+    // synchronisation, so other contexts' work keeps running
+    release_after(c->stream);
+    for (void* p : ptrs) free_idle(p);
     delete c;
 }
 

@@ -561,7 +561,7 @@ cudaError_t exact_prepare(smp_ctx* c) {
     if (c->ex_ready) return cudaSuccess;
     const int64_t want = std::max<int64_t>(c->nnz, 1);
     if (want > c->ex_cap) {
-        if (c->ex_part) cudaFreeAsync(c->ex_part, c->stream);
+        free_after(c->ex_part, c->stream);
         c->ex_part = nullptr;
         c->ex_cap = 0;
         const int64_t cap = want + want / 8 + 1024;
@@ -596,7 +596,7 @@ cudaError_t launch_exact(smp_ctx* c, const void* A, int64_t lda, const void* B, 
     const int64_t ldt = round_up_i64(c->max_rows, 4);
     const size_t at_bytes = (size_t)n1 * ldt * 4;
     if (c->ex_at_bytes < at_bytes) {
-        if (c->ex_at) cudaFreeAsync(c->ex_at, c->stream);
+        free_after(c->ex_at, c->stream);
         c->ex_at = nullptr;
         c->ex_at_bytes = 0;
         if ((e = dev_malloc((void**)&c->ex_at, at_bytes, c->stream)) != cudaSuccess) return e;

@@ -110,6 +110,16 @@ inline cudaError_t dev_malloc(T** p, size_t bytes, cudaStream_t st) {
     return cudaMallocAsync((void**)p, bytes, st);
 }
 
+// Stream-ordered frees all go to one long-lived stream per device: when frees are spread over the many short-lived
+// streams of contexts and jobs, the device memory pool's later allocations slow down several-fold.
+cudaStream_t release_stream();
+// Free memory that no queued work uses any more.
+void free_idle(void* p);
+// Order the release stream behind the work queued so far on st (then free_idle frees after that work).
+void release_after(cudaStream_t st);
+// release_after(st) + free_idle(p): for memory that work queued on st may still read.
+void free_after(void* p, cudaStream_t st);
+
 // sketch.cu
 cudaError_t launch_sketch_simt(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t row0,
                                int64_t nrows, const void* Pi, int64_t ldp);

@@ -315,7 +315,7 @@ __global__ void mn_qhat_kernel(const int32_t* __restrict__ erow, const int32_t* 
 template <typename T>
 cudaError_t ensure(T*& p, int64_t& have, int64_t need, cudaStream_t st) {
     if (have >= need && p) return cudaSuccess;
-    if (p) cudaFreeAsync(p, st);
+    free_after(p, st);
     p = nullptr;
     have = 0;
     cudaError_t e = dev_malloc((void**)&p, (size_t)std::max<int64_t>(need, 1) * sizeof(T), st);
@@ -330,8 +330,8 @@ smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out, boo
     const int64_t W = (n2 + 31) / 32;
     cudaStream_t st = c->stream;
     if (c->mask_words < n1 * W) {
-        if (c->mask) cudaFreeAsync(c->mask, st);
-        if (c->wpre) cudaFreeAsync(c->wpre, st);
+        free_after(c->mask, st);
+        free_after(c->wpre, st);
         c->mask = nullptr;
         c->wpre = nullptr;
         c->mask_words = 0;
@@ -373,7 +373,7 @@ smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out, boo
             (e = cudaStreamSynchronize(st)) != cudaSuccess)
             return check_cuda(c, e, "smp_sample_multinomial draw count");
         if (ndraw > c->mn_draw_cap) {
-            if (c->mn_draw) cudaFreeAsync(c->mn_draw, st);
+            free_after(c->mn_draw, st);
             c->mn_draw = nullptr;
             c->mn_draw_cap = 0;
             if (dev_malloc((void**)&c->mn_draw, (size_t)ndraw * 4, st) != cudaSuccess)
@@ -409,7 +409,7 @@ smp_status run_sample(smp_ctx* c, double m, uint64_t seed, int64_t* nnz_out, boo
                                                       c->csc_pos);
         if (multinomial) {
             if (nnz > c->mn_count_cap) {
-                if (c->mn_count) cudaFreeAsync(c->mn_count, st);
+                free_after(c->mn_count, st);
                 c->mn_count = nullptr;
                 c->mn_count_cap = 0;
                 if (dev_malloc((void**)&c->mn_count, (size_t)c->cap * 4, st) != cudaSuccess)

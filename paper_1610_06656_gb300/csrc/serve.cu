@@ -80,8 +80,8 @@ void solve_job(Job* j) {
     if (s == SMP_OK) s = smp_estimate(c, vals);
     if (s == SMP_OK)
         s = smp_waltmin(c, vals, j->jp.r, j->jp.T, j->jp.flags, j->jp.walt_seed, nullptr, j->U, j->S, j->V);
-    if (vals) cudaFreeAsync(vals, j->stream);
-    if (s == SMP_OK && cudaStreamSynchronize(j->stream) != cudaSuccess) s = SMP_ECUDA;
+    if (cudaStreamSynchronize(j->stream) != cudaSuccess && s == SMP_OK) s = SMP_ECUDA;
+    smp::free_idle(vals);
     j->nnz = nnz;
     j->status = s;
     if (s != SMP_OK) j->err = smp_last_error(c);
@@ -118,7 +118,7 @@ void release_job(smp_server* sv, int64_t id) {   // caller holds sv->mu; the job
     Job* j = it->second.get();
     if (j->stream) cudaStreamSynchronize(j->stream);
     if (j->ctx) smp_destroy(j->ctx);
-    if (j->U) cudaFreeAsync(j->U, j->stream);
+    smp::free_idle(j->U);   // the job's stream was synchronised above
     if (j->stream) cudaStreamDestroy(j->stream);
     sv->used -= j->bytes;
     sv->jobs.erase(it);

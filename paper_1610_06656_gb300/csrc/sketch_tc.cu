@@ -471,7 +471,7 @@ cudaError_t ensure_pi_buffers(smp_ctx* c, size_t bytes) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // no sketch still reads the old buffers
     if (e != cudaSuccess) return e;
     for (int b = 0; b < 2; ++b) {
-        if (c->pi_buf[b]) cudaFreeAsync(c->pi_buf[b], c->stream);
+        free_idle(c->pi_buf[b]);   // both streams were synchronised above
         c->pi_buf[b] = nullptr;
         c->pi_row0[b] = -1;
         c->pi_nrows[b] = 0;
@@ -604,10 +604,11 @@ cudaError_t tc_speculate_first_block(smp_ctx* c) {
 
 void release_tc(smp_ctx* c) {
     if (c->gen_stream) cudaStreamSynchronize(c->gen_stream);   // the side stream is done with the buffers
-    if (c->fp8_ws) cudaFreeAsync(c->fp8_ws, c->stream);
+    release_after(c->stream);
+    free_idle(c->fp8_ws);
     c->fp8_ws = nullptr;
     for (int b = 0; b < 2; ++b) {
-        if (c->pi_buf[b]) cudaFreeAsync(c->pi_buf[b], c->stream);
+        free_idle(c->pi_buf[b]);
         if (c->pi_ready[b]) cudaEventDestroy(c->pi_ready[b]);
         if (c->pi_free[b]) cudaEventDestroy(c->pi_free[b]);
         c->pi_buf[b] = nullptr;

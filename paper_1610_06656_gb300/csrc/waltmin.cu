@@ -872,7 +872,7 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
     cudaMemcpyAsync(&counts[1], cols_sg.start + n2, 8, cudaMemcpyDeviceToHost, st);
     cudaError_t ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) {
-        cudaFreeAsync(ws, st);
+        free_after(ws, st);
         return check_cuda(c, ce, "smp_waltmin: segment counts");
     }
     rows_sg.nseg = counts[0];
@@ -993,8 +993,8 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) status = check_cuda(c, e, "smp_waltmin kernels");
     }
-    cudaFreeAsync(ws, st);
     cudaError_t e = cudaStreamSynchronize(st);
+    free_after(ws, st);
     if (status == SMP_OK && e != cudaSuccess) status = check_cuda(c, e, "smp_waltmin sync");
     if (status == SMP_OK) status = read_device_error(c);
     return status;
@@ -1244,8 +1244,8 @@ smp_status sketch_svd_typed(smp_ctx* c, int r, uint64_t seed, double* U, double*
     }
     cudaError_t e = cudaGetLastError();
     if (status == SMP_OK && e != cudaSuccess) status = check_cuda(c, e, "smp_sketch_svd kernels");
-    cudaFreeAsync(ws, st);
     e = cudaStreamSynchronize(st);
+    free_after(ws, st);
     if (status == SMP_OK && e != cudaSuccess) status = check_cuda(c, e, "smp_sketch_svd sync");
     if (status == SMP_OK) status = read_device_error(c);
     return status;
