@@ -85,3 +85,71 @@ def test_batch_instances_and_tuner_cache(tmp_path):
     t2 = batch.EngineTuner(fake, cache_path=path)                       # reloaded from the file: no new trials
     assert t2.choose(1000, 40, S.SMP_F32) == S.SMP_ENGINE_TC and t2.trials == 0
     assert batch.n_bucket(64) == 64 and batch.n_bucket(65) == 128 and batch.n_bucket(2048) == 2048
+
+
+class _FakeServer:
+    """Stands in for libsmp's server calls: admits while a byte budget lasts, records the call order."""
+
+    def __init__(self, budget):
+        self.budget, self.used, self.next, self.log, self.live = budget, 0, 1, [], {}
+
+    def admit(self, jp):
+        need = int(jp.sketch.n1) * 1000
+        if self.used + need > self.budget:
+            return None
+        jid, self.next = self.next, self.next + 1
+        self.used += need
+        self.live[jid] = need
+        self.log.append(("admit", jid))
+        return jid
+
+    def block(self, jid, row0, nrows):
+        self.log.append(("block", jid, row0, nrows))
+
+    def close(self, jid):
+        self.log.append(("close", jid))
+
+    def collect(self, jid):
+        self.used -= self.live.pop(jid)
+        self.log.append(("collect", jid))
+        return 7, 1.5
+
+
+def test_staged_schedule_waves_and_order(monkeypatch):
+    """run_staged: a wave is what the budget admits; every block of the wave is pushed (round-robin by block index)
+    before the device sync, every job of the wave is closed after it, and the next wave starts after collection."""
+    fake = _FakeServer(budget=2500 * 1000)
+    monkeypatch.setattr(S, "smp_serve_admit", lambda sv, jp: fake.admit(jp))
+    monkeypatch.setattr(S, "smp_serve_block", lambda sv, jid, a, lda, b, ldb, r0, nr: fake.block(jid, r0, nr))
+    monkeypatch.setattr(S, "smp_serve_close", lambda sv, jid: fake.close(jid))
+    monkeypatch.setattr(S, "smp_serve_collect", lambda sv, jid, U=None, Sv=None, V=None: fake.collect(jid))
+    syncs = []
+    fake_sync = lambda: (syncs.append(len(fake.log)), fake.log.append(("sync",)))   # noqa: E731
+
+    class Pool:
+        def __init__(self):
+            self.shape = (1_000_000, 2048)
+
+        def stride(self, i):
+            return 2048
+
+        def __getitem__(self, idx):
+            return None
+
+    jobs = [serve.JobSpec(i, 0.0, n, d, 5, 40, 10, 1000.0, 0, i)
+            for i, (n, d) in enumerate([(1000, 70000), (1000, 10000), (1000, 40000), (800, 32768)])]
+    recs, wall = serve.run_staged(None, jobs, Pool(), Pool(), S.SMP_F32, block_rows=32768, sync=fake_sync)
+    assert [r["idx"] for r in recs] == [0, 1, 2, 3] and all(r["nnz"] == 7 for r in recs)
+    ev = fake.log
+    # wave 1: jobs 1, 2 (2,000 of the 2,500 budget; job 3 would exceed it); wave 2: jobs 3, 4
+    assert [e for e in ev if e[0] == "admit"] == [("admit", 1), ("admit", 2), ("admit", 3), ("admit", 4)]
+    s1, s2 = [i for i, e in enumerate(ev) if e[0] == "sync"]
+    w1 = ev[:s1]
+    assert [e for e in w1 if e[0] == "block"] == [("block", 1, 0, 32768), ("block", 2, 0, 10000),
+                                                 ("block", 1, 32768, 32768), ("block", 1, 65536, 4464)]
+    assert all(e[0] in ("admit", "block") for e in w1) and ("admit", 3) not in w1
+    w1_after = ev[s1 + 1:s2]
+    assert w1_after[:2] == [("close", 1), ("close", 2)] and ("collect", 2) in w1_after
+    assert w1_after.index(("collect", 2)) < w1_after.index(("admit", 3))
+    assert ev[-2:] == [("collect", 3), ("collect", 4)]
+    assert fake.used == 0
