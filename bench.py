@@ -206,6 +206,8 @@ def main():
     ap.add_argument("--no-error", action="store_true")
     ap.add_argument("--workers", type=int, default=0, help="solve worker threads of the batched / serving forms")
     ap.add_argument("--batch-dtype", default="f32", choices=["f32", "bf16"], help="stored inputs of the batched form")
+    ap.add_argument("--serve-dtype", default="bf16", choices=["f32", "bf16"], help="stored inputs of the serving form")
+    ap.add_argument("--rate", type=float, default=0.0, help="serving form: offered jobs/s instead of 200")
     ap.add_argument("--size", type=int, default=0, help="table1 workload: d = n = SIZE instead of 100,000")
     ap.add_argument("--no-baseline", action="store_true",
                     help="skip the SVD(A~^T B~) and multinomial-sampling comparisons")
@@ -608,33 +610,37 @@ def run_serving(args, w):
     from paper_1610_06656_gb300 import build, serve, smp, synth
     smp.load(build.build())
     torch.cuda.set_device(0)
+    f32 = args.serve_dtype == "f32"
+    tdt, sdt, esz = (torch.float32, smp.SMP_F32, 4) if f32 else (torch.bfloat16, smp.SMP_BF16, 2)
+    if args.rate:
+        w = dict(w, rate=args.rate)
     pool_A, pool_B, _, _, _ = synth.lowrank_plus_noise_torch(w["pool_rows"], w["width"], w["width"], w["L"],
                                                              w["sigma"], w["alpha"], seed=1005, device="cuda",
-                                                             dtype=torch.bfloat16)
+                                                             dtype=tdt)
     torch.cuda.synchronize()
-    pool_bytes = 2 * pool_A.numel() * 2
+    pool_bytes = 2 * pool_A.numel() * esz
     workers = args.workers or w["workers"]
     server = smp.smp_serve_create(int(w["budget"] - pool_bytes), solve_workers=workers)
     try:
         warm = serve.poisson_jobs(w["warm_jobs"], w["rate"], seed=99, pool_rows=w["pool_rows"], T=w["T"])
-        serve.run(server, warm, pool_A, pool_B, smp.SMP_BF16, block_rows=w["block"])
+        serve.run(server, warm, pool_A, pool_B, sdt, block_rows=w["block"])
         jobs = serve.poisson_jobs(w["jobs"], w["rate"], seed=5, pool_rows=w["pool_rows"], T=w["T"])
         clocks = ClockSampler(0)
         clocks.start()
         launches0 = smp.smp_launch_count()
-        records, wall = serve.run(server, jobs, pool_A, pool_B, smp.SMP_BF16, block_rows=w["block"])
+        records, wall = serve.run(server, jobs, pool_A, pool_B, sdt, block_rows=w["block"])
         launches = smp.smp_launch_count() - launches0
         clk = clocks.stop()
     finally:
         smp.smp_serve_destroy(server)
     lat = sorted(r["latency_ms"] for r in records)
-    streamed = sum(j.d * 2 * j.n * 2 for j in jobs)
+    streamed = sum(j.d * 2 * j.n * esz for j in jobs)
     line = {"metric": "serving: completed solves/s under Poisson arrivals; p50/p99 latency from a job's last "
                       "block to its factors", "value": len(records) / wall, "unit": "solves/s", "n_gpus": 1,
             "steps": len(records), "warmup": w["warm_jobs"], "ms_per_step": 1e3 * wall / max(1, len(records)),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.serve_dtype,
             "data": "synthetic (low rank 20 + noise 0.1, column scales (j+1)^-0.5), job inputs are windows of a "
-                    "resident %d x %d BF16 pool pair" % (w["pool_rows"], w["width"]),
+                    "resident %d x %d %s pool pair" % (w["pool_rows"], w["width"], "FP32" if f32 else "BF16"),
             "config": {"workload": "serve", "arrival_rate_per_s": w["rate"], "jobs": w["jobs"],
                        "n": "uniform [64, 2048]", "d": "uniform [10000, 500000]", "r": [5, 10, 20], "k": "8 r",
                        "T": w["T"], "block_rows": w["block"], "budget_bytes": w["budget"],
