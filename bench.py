@@ -38,7 +38,7 @@ WORKLOADS = {
     # precision form: BF16-stored inputs, sketch in BF16 and in FP8 E4M3 (tensor cores) against the FP32 path
     # (k = 1,024 exceeds the TF32 engine's 512, so FP32 runs on the CUDA-core engine) on the same stored values
     "precision": dict(d=4_000_000, n1=4096, n2=4096, L=32, sigma=0.05, alpha=0.7, k=1024, r=20, T=15, block=65536,
-                      steps=2, warm=1),
+                      steps=4, warm=1),
     # one 65,536-row block of the precision shape (1 GB of BF16 inputs): the case the ncu captures use
     "precision_block": dict(d=65536, n1=4096, n2=4096, L=32, sigma=0.05, alpha=0.7, k=1024, r=20, T=15,
                             block=65536, steps=1, warm=1),
@@ -671,30 +671,51 @@ def run_precision(args, w):
     factors = []
     for name, tdt, eng in forms:
         Xa, Xb = (A, B) if tdt == torch.bfloat16 else (A.float(), B.float())
-        solver = pipeline.Solver(w["n1"], w["n2"], w["k"], tdt, seed=1, engine=eng, max_rows=w["block"])
-        sk_ms = []
+        # two contexts on two streams, consecutive solves alternating: solve i + 1's sketch runs while solve i's
+        # WAltMin finishes (as in the scale bench)
+        sts = [torch.cuda.Stream() for _ in range(2)]
+        svs = [pipeline.Solver(w["n1"], w["n2"], w["k"], tdt, seed=1, engine=eng, max_rows=w["block"],
+                               stream=st.cuda_stream) for st in sts]
+        sk_ev = []
 
-        def step():
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            solver.sketch(Xa, Xb, w["block"])
-            e1.record(stream)
-            nnz = solver.sample(m, 2)
-            out = solver.waltmin(solver.estimate(nnz), w["r"], w["T"], 0, 3)
-            sk_ms.append(e0.elapsed_time(e1))
-            return out, nnz
+        def run(count):
+            out = None
 
-        for _ in range(w["warm"]):
-            step()
+            def issue(i):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(sts[i % 2])
+                svs[i % 2].sketch(Xa, Xb, w["block"])
+                e1.record(sts[i % 2])
+                sk_ev.append((e0, e1))
+
+            issue(0)
+            for i in range(count):
+                sv, st = svs[i % 2], sts[i % 2]
+                nnz = sv.sample(m, 2)
+                with torch.cuda.stream(st):
+                    vals = sv.estimate(nnz)
+                if i + 1 < count:
+                    issue(i + 1)
+                with torch.cuda.stream(st):
+                    out = sv.waltmin(vals, w["r"], w["T"], 0, 3), nnz
+            return out
+
+        run(w["warm"])
         torch.cuda.synchronize()
-        sk_ms.clear()
+        sk_ev.clear()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
-        for _ in range(w["steps"]):
-            (U, S, V), nnz = step()
+        for st in sts:
+            st.wait_event(t0)
+        (U, S, V), nnz = run(w["steps"])
+        for st in sts:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            stream.wait_event(ev)
         t1.record(stream)
         torch.cuda.synchronize()
+        sk_ms = [a.elapsed_time(b) for a, b in sk_ev]
         ms = t0.elapsed_time(t1) / w["steps"]
         in_bytes = w["d"] * (w["n1"] + w["n2"]) * (2 if tdt == torch.bfloat16 else 4)
         flops = 2.0 * w["k"] * w["d"] * (w["n1"] + w["n2"])
@@ -702,7 +723,8 @@ def run_precision(args, w):
                          "sketch_tflops": flops / (sum(sk_ms) / len(sk_ms)) / 1e9,
                          "sketch_gbs": in_bytes / (sum(sk_ms) / len(sk_ms)) / 1e6, "nnz": int(nnz)}
         factors.append((U.clone(), S.clone(), V.clone()))
-        solver.close()
+        for sv in svs:
+            sv.close()
         del Xa, Xb
         torch.cuda.empty_cache()
     opt = None
