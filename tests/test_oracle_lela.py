@@ -93,3 +93,21 @@ def test_table1_ordering_on_the_tiny_workload():
     e_s = smp.spectral_error(M, s["U"], s["S"], s["V"])
     assert opt - 1e-12 <= e_l <= 1.01 * opt
     assert e_l < e_s
+
+
+def test_table1_ordering_on_the_gd_model():
+    """Table 1's generator, A = B = G D (D_ii = 1 / i, one shared G), at d = n = 1,000 with r = 5, T = 10 and
+    m = 4 n r ln n: LELA's exact entries reach the Eckart-Young optimum (sigma_6 / sigma_1, near 1 / 36), and
+    SMP-PCA with k = 200 stays above LELA, the ordering Table 1 prints for d = n = 100,000."""
+    n, r = 1000, 5
+    A = synth.gd(n, n, seed=7)
+    M = A.T @ A
+    opt = smp.optimal_error(M, r)
+    assert 0.025 < opt < 1.0 / 30
+    m = smp.default_m(n, n, r)
+    l = smp.lela(A, None, r, m, 10, sample_seed=2, same_ab=True)
+    s = smp.smp_pca(A, None, r, 200, m, 10, seed=1, sample_seed=2, same_ab=True)
+    e_l = smp.spectral_error(M, l["U"], l["S"], l["V"])
+    e_s = smp.spectral_error(M, s["U"], s["S"], s["V"])
+    assert opt - 1e-12 <= e_l <= opt * (1 + 1e-4)
+    assert e_l < e_s
