@@ -111,3 +111,26 @@ def test_table1_ordering_on_the_gd_model():
     e_s = smp.spectral_error(M, s["U"], s["S"], s["V"])
     assert opt - 1e-12 <= e_l <= opt * (1 + 1e-4)
     assert e_l < e_s
+
+
+def test_gd_generator_scaling():
+    """synth.gd is G D with D_ii = 1 / i: column i of A / (1 / i) is a standard Gaussian column (mean 0, variance
+    1), and the squared column norms fall as d / i^2."""
+    d, n = 4000, 50
+    A = synth.gd(d, n, seed=5)
+    G = A * np.arange(1, n + 1)
+    assert abs(G.mean()) < 0.01 and abs(G.var() - 1.0) < 0.02
+    sq = (A ** 2).sum(0)
+    np.testing.assert_allclose(sq * np.arange(1, n + 1) ** 2 / d, 1.0, atol=0.12)
+
+
+def test_lela_with_multinomial_sampling():
+    """LELA on the Appendix's row-wise multinomial Omega: the same draws as the SMP-PCA oracle makes for the same
+    norms, and with a generous budget an exactly rank-r product is recovered."""
+    d, n, r = 40, 20, 2
+    A, B = synth.lowrank_plus_noise(d, n, n, r, 0.0, 0.5, seed=23, dtype=np.float64)
+    m = 40.0 * n * r
+    out = smp.lela(A, B, r, m, 10, sample_seed=4, sampler="multinomial")
+    rows, cols, qhat, _ = smp.sample_omega_multinomial(*smp.column_norms_sq(A, B), m, 4)
+    assert np.array_equal(out["rows"], rows) and np.array_equal(out["cols"], cols)
+    assert smp.spectral_error(A.T @ B, out["U"], out["S"], out["V"]) < 1e-6
