@@ -110,9 +110,11 @@ smp_status smp_sketch_begin(const smp_params* params, void* stream, smp_ctx** ou
 
 /* Add the contribution of data rows [row0, row0 + nrows): At += Pi[:, rows] A_blk, Bt += Pi[:, rows] B_blk and the
  * squares of every entry to the column sums (Algorithm 1, step 2; Section 2.1 "Step 1"). Pi(a, t) ~ N(0, 1/k) is
- * never stored: it is generated from Philox counter (t mod 2^32, t >> 32, a / 4, 1) with a Box-Muller map
- * (words 0,1 -> rows 4g, 4g+1; words 2,3 -> rows 4g+2, 4g+3; u1 = ((x>>8)+1) 2^-24, u2 = (x>>8) 2^-24,
- * rho = sqrt(-2 ln u1), z = rho cos(2 pi u2), rho sin(2 pi u2), Pi = z / sqrt(k)).
+ * generated from Philox counter (t mod 2^32, t >> 32, a / 4, 1) with a Box-Muller map (words 0,1 -> rows 4g, 4g+1;
+ * words 2,3 -> rows 4g+2, 4g+3; u1 = ((x>>8)+1) 2^-24, u2 = (x>>8) 2^-24, rho = sqrt(-2 ln u1),
+ * z = rho cos(2 pi u2), rho sin(2 pi u2), Pi = z / sqrt(k)) and never kept beyond the block: the CUDA-core engine
+ * generates it in registers; the tensor-core engines generate the block's k x nrows slice once, in the operand
+ * type, into a context buffer that every column tile of the block reads (and that the next block overwrites).
  * A_blk_dev / B_blk_dev: device, row-major, element type from params.dtype, lda >= n1, ldb >= n2; B ignored when
  * same_ab. 0 <= nrows <= max_rows; nrows = 0 is a no-op. Blocks may arrive in any order; a block overlapping
  * rows already accumulated since the context was created or reset is rejected (SMP_EINVAL) before anything is
@@ -120,6 +122,18 @@ smp_status smp_sketch_begin(const smp_params* params, void* stream, smp_ctx** ou
  * SMP_ECUDA. */
 smp_status smp_sketch_accumulate(smp_ctx* ctx, const void* A_blk_dev, int64_t lda, const void* B_blk_dev,
                                  int64_t ldb, int64_t row0, int64_t nrows);
+
+/* smp_sketch_accumulate for a row block held in HOST memory: A_blk_host (nrows x n1, leading dimension lda) and
+ * B_blk_host (nrows x n2, ldb; ignored when same_ab) are copied into one of two context-owned device staging
+ * buffers (max_rows x (n1 + n2) elements, rows padded to 16 bytes, allocated on the first call) on a copy stream of
+ * the context, and the block is then sketched from there on the context's stream exactly as smp_sketch_accumulate
+ * would (same engines, checks and results). Consecutive calls alternate between the two buffers, so the copy of one
+ * block overlaps the sketch of the previous one. The copy overlaps the caller's host work only for page-locked
+ * (pinned) host memory; pageable memory is staged by the CUDA runtime. The host block must stay valid and unchanged
+ * until the context's stream has been synchronised (smp_sync, smp_sample, smp_waltmin). Asynchronous. Errors: as
+ * smp_sketch_accumulate; SMP_ENOMEM (staging buffers). */
+smp_status smp_sketch_accumulate_host(smp_ctx* ctx, const void* A_blk_host, int64_t lda, const void* B_blk_host,
+                                      int64_t ldb, int64_t row0, int64_t nrows);
 
 /* Same as smp_sketch_accumulate but with Pi[:, row0:row0+nrows] supplied by the caller (test hook: Pi = I, or
  * the oracle's Pi). Pi_blk_dev is k x nrows row-major with leading dimension ldp, element type float (double for
@@ -308,14 +322,15 @@ int32_t smp_version(void);
  * Philox Pi, same SIMT kernel) and writes it to the caller's device buffers: At_dev (n1 x k row-major, row i =
  * sketch column At_i), Bt_dev (n2 x k), sA_dev (n1 doubles, ||A_i||^2 over the range) and sB_dev (n2 doubles).
  * A_dev / B_dev: nrows x n1 / nrows x n2 row-major, lda >= n1, ldb >= n2, dtype SMP_F32 or SMP_BF16 (others:
- * SMP_EUNSUPPORTED). Asynchronous on stream (a cudaStream_t).
+ * SMP_EUNSUPPORTED). 1 <= n1, n2 <= 2^30, 1 <= k <= 1024. Asynchronous on stream (a cudaStream_t).
  * Scratch: a fixed array of SMP_NOALLOC_SCRATCH_BYTES (16 MiB) compiled into the library, held on every GPU that
  * loads it until the process exits. The partials need (n1 + n2) * (round_up(k, 4) * 4 + 8) bytes (each part rounded
  * up to 256 bytes); larger shapes are rejected with SMP_EINVAL before anything is launched. The call performs no
- * cudaMalloc / cudaFree. The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current and caches it: make that first call before any stream capture. Every call on a device
- * shares the one array and clears the part it uses, so calls whose work overlaps on the GPU (other streams, other
- * host threads) race and must be serialised by the caller. */
+ * cudaMalloc / cudaFree. The first call in a CUDA context looks up the array's device address
+ * (cudaGetSymbolAddress) in that context and caches it under the context's unique id (so a device reset or a second
+ * context on the same device gets a lookup of its own): make that first call before any stream capture. Every call
+ * on a device shares the one array and clears the part it uses, so calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller. */
 #define SMP_NOALLOC_SCRATCH_BYTES (16u << 20)
 smp_status smp_sketch_noalloc(const void* A_dev, int64_t lda, const void* B_dev, int64_t ldb, int64_t n1,
                               int64_t n2, int32_t k, int32_t dtype, uint64_t seed, int64_t row0, int64_t nrows,
@@ -366,6 +381,16 @@ smp_status smp_exact_coverage(const smp_ctx* ctx, int64_t* rows, int64_t* first_
 /* Fault injection for tests: the next n device allocations made by the library fail (the calls that made them
  * return SMP_ENOMEM and leave the context usable or destroyable). n <= 0 clears it. Process-wide. */
 void smp_debug_fail_allocs(int32_t n);
+
+/* Test hook of the bounded device-side waits (failure detection; the paper has no counterpart):
+ * every mbarrier wait of the TF32 / BF16-operand tensor-core sketch kernel (SMP_ENGINE_TC with SMP_F32 blocks,
+ * SMP_ENGINE_TC_BF16) gives up after wait_ns nanoseconds (<= 0: the default of 2 s); if skip_stage >= 0, the next
+ * such launch issues no data loads from pipeline stage skip_stage on, so the waits on that stage run out: the
+ * kernel then records DEVERR_TIMEOUT in the context's error word, lets its loads and MMAs in flight finish, frees
+ * its tensor memory and returns, the next synchronising call returns SMP_ETIMEOUT, and the context stays usable
+ * (smp_sketch_reset, then accumulate again). The skip applies to one launch; the limit stays until changed.
+ * Process-wide. */
+void smp_debug_tc_wait(int64_t wait_ns, int32_t skip_stage);
 
 #ifdef __cplusplus
 }

@@ -21,6 +21,8 @@ namespace smp {
 
 std::atomic<uint64_t> g_launches{0};
 std::atomic<int32_t> g_fail_allocs{0};
+std::atomic<int64_t> g_tc_wait_ns{0};
+std::atomic<int32_t> g_tc_skip_stage{-1};
 
 cudaStream_t release_stream() {
     static std::mutex mu;
@@ -89,7 +91,23 @@ using namespace smp;
 
 namespace {
 
+void release_host_stage(smp_ctx* c) {
+    if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+    release_after(c->stream);
+    for (int b = 0; b < 2; ++b) {
+        free_idle(c->host_stage[b]);
+        if (c->host_copied[b]) cudaEventDestroy(c->host_copied[b]);
+        if (c->host_consumed[b]) cudaEventDestroy(c->host_consumed[b]);
+        c->host_stage[b] = nullptr;
+        c->host_copied[b] = c->host_consumed[b] = nullptr;
+    }
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    c->copy_stream = nullptr;
+    c->host_stage_bytes = 0;
+}
+
 void free_ctx(smp_ctx* c) {
+    release_host_stage(c);
     release_tc(c);
     void* ptrs[] = {c->part,   c->nsq,    c->sk,      c->s_all,   c->D_all,   c->F,     c->row_ptr, c->col_ptr,
                     c->col,    c->qhat,   c->csc_row, c->csc_pos, c->alpha,   c->beta,  c->mask,    c->wpre,
@@ -298,6 +316,62 @@ smp_status smp_sketch_accumulate(smp_ctx* c, const void* A, int64_t lda, const v
                              : bf16 ? launch_sketch_bf16(c, A, lda, B, ldb, row0, nrows, nullptr, 0)
                                     : launch_sketch_tc(c, A, lda, B, ldb, row0, nrows);
     return check_cuda(c, e, "smp_sketch_accumulate");
+}
+
+smp_status smp_sketch_accumulate_host(smp_ctx* c, const void* A, int64_t lda, const void* B, int64_t ldb,
+                                      int64_t row0, int64_t nrows) {
+    smp_status s = check_block(c, A, lda, B, ldb, nrows);
+    if (s != SMP_OK || nrows == 0) return s;
+    if (row0 < 0) return fail(c, SMP_EINVAL, "row0 < 0");
+    size_t esz = 0;
+    elem_size(c->p.dtype, &esz);
+    // staging rows padded to 16 bytes, so every engine's alignment rule holds for the device copy
+    const int64_t pitch_a = round_up(c->p.n1, (int64_t)(16 / esz));
+    const int64_t pitch_b = c->p.same_ab ? 0 : round_up(c->p.n2, (int64_t)(16 / esz));
+    const size_t bytes = (size_t)c->max_rows * (size_t)(pitch_a + pitch_b) * esz;
+    cudaError_t e = cudaSuccess;
+    if (!c->copy_stream) {
+        e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = cudaEventCreateWithFlags(&c->host_copied[b], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->host_consumed[b], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return check_cuda(c, e, "smp_sketch_accumulate_host: copy stream");
+    }
+    if (c->host_stage_bytes < bytes) {
+        for (int b = 0; b < 2; ++b) {
+            free_after(c->host_stage[b], c->stream);
+            c->host_stage[b] = nullptr;
+        }
+        c->host_stage_bytes = 0;
+        for (int b = 0; b < 2; ++b) {
+            if (smp::dev_malloc(&c->host_stage[b], bytes, c->stream) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(c, SMP_ENOMEM, "smp_sketch_accumulate_host: staging buffers");
+            }
+            if ((e = cudaEventRecord(c->host_consumed[b], c->stream)) != cudaSuccess)
+                return check_cuda(c, e, "smp_sketch_accumulate_host");
+        }
+        c->host_stage_bytes = bytes;
+    }
+    const int b = c->host_next;
+    char* dA = (char*)c->host_stage[b];
+    char* dB = dA + (size_t)c->max_rows * pitch_a * esz;
+    e = cudaStreamWaitEvent(c->copy_stream, c->host_consumed[b], 0);   // the sketch that last read buffer b ended
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(dA, pitch_a * esz, A, lda * esz, c->p.n1 * esz, nrows, cudaMemcpyHostToDevice,
+                              c->copy_stream);
+    if (e == cudaSuccess && !c->p.same_ab)
+        e = cudaMemcpy2DAsync(dB, pitch_b * esz, B, ldb * esz, c->p.n2 * esz, nrows, cudaMemcpyHostToDevice,
+                              c->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->host_copied[b], c->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->host_copied[b], 0);
+    if (e != cudaSuccess) return check_cuda(c, e, "smp_sketch_accumulate_host: host-to-device copy");
+    s = smp_sketch_accumulate(c, dA, pitch_a, c->p.same_ab ? nullptr : dB, pitch_b, row0, nrows);
+    e = cudaEventRecord(c->host_consumed[b], c->stream);
+    c->host_next = 1 - b;
+    if (s != SMP_OK) return s;
+    return check_cuda(c, e, "smp_sketch_accumulate_host");
 }
 
 smp_status smp_sketch_accumulate_pi(smp_ctx* c, const void* Pi, int64_t ldp, const void* A, int64_t lda,
@@ -552,6 +626,11 @@ int32_t smp_version(void) { return 100; }
 int64_t smp_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
 void smp_debug_fail_allocs(int32_t n) { g_fail_allocs.store(n > 0 ? n : 0, std::memory_order_relaxed); }
+
+void smp_debug_tc_wait(int64_t wait_ns, int32_t skip_stage) {
+    g_tc_wait_ns.store(wait_ns > 0 ? wait_ns : 0, std::memory_order_relaxed);
+    g_tc_skip_stage.store(skip_stage >= 0 ? skip_stage : -1, std::memory_order_relaxed);
+}
 
 smp_status smp_sketch_coverage(const smp_ctx* c, int64_t* rows, int64_t* first_missing, int64_t* ranges) {
     if (!c) return fail(nullptr, SMP_EINVAL, "null context");

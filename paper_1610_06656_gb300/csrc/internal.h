@@ -80,6 +80,14 @@ struct smp_ctx {
     float* ex_at = nullptr;          // [n1][max_rows rounded up to 4] TF32 A^T of the current row block
     size_t ex_at_bytes = 0;
     std::vector<std::pair<int64_t, int64_t>> seen_exact;   // row ranges of the second pass since Omega was drawn
+    // host-resident row blocks (smp_sketch_accumulate_host, allocated on first use): two device staging buffers
+    // filled on a copy stream, so the copy of block i + 1 overlaps the sketch of block i
+    void* host_stage[2] = {nullptr, nullptr};
+    size_t host_stage_bytes = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t host_copied[2] = {nullptr, nullptr};     // recorded on copy_stream after a buffer's copy
+    cudaEvent_t host_consumed[2] = {nullptr, nullptr};   // recorded on stream after the sketch that read a buffer
+    int host_next = 0;
     std::string err;
 };
 
@@ -98,6 +106,10 @@ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 // Device allocations of the library (stream-ordered). smp_debug_fail_allocs(n) makes the next n of them fail with
 // cudaErrorMemoryAllocation: host-side fault injection for the SMP_ENOMEM paths.
 extern std::atomic<int32_t> g_fail_allocs;
+// Test hooks of the tensor-core sketch engines' bounded waits (smp_debug_tc_wait): the wait limit in ns (0: the
+// 2 s default) and a stage whose data loads the next launch does not issue (-1: none; consumed by that launch).
+extern std::atomic<int64_t> g_tc_wait_ns;
+extern std::atomic<int32_t> g_tc_skip_stage;
 template <typename T>
 inline cudaError_t dev_malloc(T** p, size_t bytes, cudaStream_t st) {
     int32_t left = g_fail_allocs.load(std::memory_order_relaxed);
@@ -126,6 +138,9 @@ cudaError_t launch_sketch_simt(smp_ctx* c, const void* A, int64_t lda, const voi
 cudaError_t launch_finalize(smp_ctx* c);
 cudaError_t launch_frobenius(smp_ctx* c);   // F[0], F[1] from s_all (left-to-right sums)
 cudaError_t launch_import(smp_ctx* c, const void* At, const void* Bt, const double* sA, const double* sB);
+// Row splits the SIMT engine uses for a row range of nrows rows when at most `splits` partials are available: the
+// `splits` argument launch_sketch_simt_into needs to touch exactly the partials it writes.
+int simt_into_splits(int64_t ntot, int k, int64_t nrows, int splits, int sm_count);
 cudaError_t launch_sketch_simt_into(int dtype, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1,
                                     int64_t n2, int k, uint64_t seed, int64_t row0, int64_t nrows, float* part,
                                     double* nsq, int splits, int sm_count, float* At, float* Bt, double* sA,

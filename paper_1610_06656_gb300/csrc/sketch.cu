@@ -383,9 +383,7 @@ cudaError_t sketch_into_typed(const void* A, int64_t lda, const void* B, int64_t
     a.row0 = row0;
     a.nrows = nrows;
     const int64_t steps = (nrows + TR - 1) / TR;
-    const int64_t tiles = ((a.ntot + TN - 1) / TN) * ((k + TK - 1) / TK);
-    int used = (int)std::min<int64_t>(splits, std::max<int64_t>(1, (2 * sm_count + tiles - 1) / tiles));
-    used = (int)std::min<int64_t>(used, std::max<int64_t>(1, steps));
+    const int used = simt_into_splits(a.ntot, k, nrows, splits, sm_count);
     a.rows_per_split = ((steps + used - 1) / used) * TR;
     a.k = k;
     a.ldk = round_up(k, 4);
@@ -400,6 +398,13 @@ cudaError_t sketch_into_typed(const void* A, int64_t lda, const void* B, int64_t
 }
 
 }  // namespace
+
+int simt_into_splits(int64_t ntot, int k, int64_t nrows, int splits, int sm_count) {
+    const int64_t steps = (nrows + TR - 1) / TR;
+    const int64_t tiles = ((ntot + TN - 1) / TN) * ((k + TK - 1) / TK);
+    int used = (int)std::min<int64_t>(splits, std::max<int64_t>(1, (2 * sm_count + tiles - 1) / tiles));
+    return (int)std::min<int64_t>(used, std::max<int64_t>(1, steps));
+}
 
 cudaError_t launch_sketch_simt_into(int dtype, const void* A, int64_t lda, const void* B, int64_t ldb, int64_t n1,
                                     int64_t n2, int k, uint64_t seed, int64_t row0, int64_t nrows, float* part,

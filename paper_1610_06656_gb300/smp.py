@@ -43,6 +43,7 @@ SIGNATURES = {
     "smp_exact_values": (_i32, [_vp, _vp]),
     "smp_exact_coverage": (_i32, [_vp, _c.POINTER(_i64), _c.POINTER(_i64), _c.POINTER(_i64)]),
     "smp_debug_fail_allocs": (None, [_i32]),
+    "smp_debug_tc_wait": (None, [_i64, _i32]),
     "smp_serve_job_bytes": (_i32, [_c.POINTER(smp_job_params), _c.POINTER(_i64)]),
     "smp_serve_create": (_i32, [_c.POINTER(smp_server_params), _c.POINTER(_vp)]),
     "smp_serve_admit": (_i32, [_vp, _c.POINTER(smp_job_params), _c.POINTER(_i64)]),
@@ -55,6 +56,7 @@ SIGNATURES = {
     "smp_serve_destroy": (_i32, [_vp]),
     "smp_sketch_begin": (_i32, [_c.POINTER(smp_params), _vp, _c.POINTER(_vp)]),
     "smp_sketch_accumulate": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _i64]),
+    "smp_sketch_accumulate_host": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _i64]),
     "smp_sketch_accumulate_pi": (_i32, [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64]),
     "smp_sketch_reset": (_i32, [_vp]),
     "smp_sketch_finalize": (_i32, [_vp]),
@@ -145,6 +147,12 @@ def smp_sketch_begin(n1, n2, k, seed, dtype=SMP_F32, same_ab=False, engine=SMP_E
 def smp_sketch_accumulate(ctx, A_blk, lda, B_blk, ldb, row0, nrows):
     _check(load().smp_sketch_accumulate(ctx, _ptr(A_blk), lda, _ptr(B_blk), ldb, row0, nrows),
            "smp_sketch_accumulate", ctx)
+
+
+def smp_sketch_accumulate_host(ctx, A_blk, lda, B_blk, ldb, row0, nrows):
+    """A_blk / B_blk: host buffers (CPU torch tensors, pinned for overlap, or raw host addresses)."""
+    _check(load().smp_sketch_accumulate_host(ctx, _ptr(A_blk), lda, _ptr(B_blk), ldb, row0, nrows),
+           "smp_sketch_accumulate_host", ctx)
 
 
 def smp_sketch_accumulate_pi(ctx, Pi_blk, ldp, A_blk, lda, B_blk, ldb, row0, nrows):
@@ -346,3 +354,7 @@ def smp_exact_coverage(ctx):
 
 def smp_debug_fail_allocs(n):
     load().smp_debug_fail_allocs(int(n))
+
+
+def smp_debug_tc_wait(wait_ns=0, skip_stage=-1):
+    load().smp_debug_tc_wait(int(wait_ns), int(skip_stage))

@@ -77,22 +77,24 @@ def test_bf16_philox_sketch_matches_oracle(env, k):
     s.close()
 
 
-def test_bf16_tc_matches_simt(env):
-    """The precision form's sketch size k = 1,024 on 2,048 rows: tensor-core engine against the CUDA-core one."""
+def test_bf16_k1024_matches_oracle(env):
+    """The precision form's sketch size k = 1,024 (two CTAs per column tile) on one 2,048-row block, against the
+    oracle run on the same stored BF16 values."""
     torch, smp, pipeline = env
     A, B = synth.lowrank_plus_noise(2048, 256, 128, 20, 0.05, 0.7, seed=7, dtype=np.float32)
     Ab, Bb = _bf16(torch, A), _bf16(torch, B)
-    out = {}
-    for name, eng in (("tc", smp.SMP_ENGINE_TC), ("simt", smp.SMP_ENGINE_SIMT)):
-        s = pipeline.Solver(256, 128, 1024, torch.bfloat16, seed=21, engine=eng, max_rows=2048)
-        s.sketch(Ab, Bb, 2048)
-        smp.smp_sync(s.ctx)
-        st = s.sketch_state()
-        out[name] = {key: st[key].cpu().numpy().astype(np.float64) for key in ("At", "Bt", "sA", "sB")}
-        s.close()
-    assert _colrel(out["tc"]["At"], out["simt"]["At"]) < 1e-2
-    assert _colrel(out["tc"]["Bt"], out["simt"]["Bt"]) < 1e-2
-    np.testing.assert_allclose(out["tc"]["sA"], out["simt"]["sA"], rtol=1e-12)
+    A64 = Ab.float().cpu().numpy().astype(np.float64)
+    B64 = Bb.float().cpu().numpy().astype(np.float64)
+    s = pipeline.Solver(256, 128, 1024, torch.bfloat16, seed=21, engine=smp.SMP_ENGINE_TC, max_rows=2048)
+    s.sketch(Ab, Bb, 2048)
+    smp.smp_sync(s.ctx)
+    st = s.sketch_state()
+    ref = O.sketch(A64, B64, 1024, 21, block_rows=2048)
+    assert _colrel(st["At"].cpu().numpy().astype(np.float64), ref.At.T) < 1e-2
+    assert _colrel(st["Bt"].cpu().numpy().astype(np.float64), ref.Bt.T) < 1e-2
+    np.testing.assert_allclose(st["sA"].cpu().numpy(), ref.sA, rtol=1e-12)
+    np.testing.assert_allclose(st["sB"].cpu().numpy(), ref.sB, rtol=1e-12)
+    s.close()
 
 
 def test_bf16_end_to_end_tiny(env):

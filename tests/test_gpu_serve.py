@@ -1,9 +1,11 @@
 """The serving form on the GPU: a job's factors are the same bits alone, in a mix of interleaved jobs and through
-the plain pipeline; admission by budget, cancellation and collection."""
+the plain pipeline, and within the stated tolerance of the CPU oracle's; admission by budget, cancellation and
+collection. The batched form: one instance bit-equal to the plain pipeline and within tolerance of the oracle."""
 import numpy as np
 import pytest
 import torch
 
+from oracle import smp as O
 from paper_1610_06656_gb300 import serve, synth
 from tests.gpu_helpers import build_lib, torch_cuda
 
@@ -23,6 +25,21 @@ def env():
 def _factors(n, r):
     return (torch.empty(n, r, dtype=torch.float64, device="cuda"), torch.empty(r, dtype=torch.float64, device="cuda"),
             torch.empty(n, r, dtype=torch.float64, device="cuda"))
+
+
+def _oracle_check(spec, A, B, factors, tol, block_rows):
+    """The job's window through the CPU oracle (binary64, on the stored values, the job's seeds): Omega's size must
+    match and the spectral error of the served factors must be within tol of the oracle's."""
+    a = A[spec.row_offset:spec.row_offset + spec.d, :spec.n].float().cpu().numpy().astype(np.float64)
+    b = B[spec.row_offset:spec.row_offset + spec.d, :spec.n].float().cpu().numpy().astype(np.float64)
+    ref = O.smp_pca(a, b, spec.r, spec.k, spec.m, spec.T, seed=2 * spec.seed + 1, sample_seed=2 * spec.seed + 2,
+                    block_rows=block_rows)
+    M = a.T @ b
+    U, S, V = (x.cpu().numpy() for x in factors)
+    e_gpu = O.spectral_error(M, U, S, V)
+    e_ref = O.spectral_error(M, ref["U"], ref["S"], ref["V"])
+    assert abs(e_gpu - e_ref) <= tol, (e_gpu, e_ref)
+    return ref
 
 
 def _jobs(count, seed):
@@ -46,6 +63,8 @@ def test_alone_mixed_and_plain_agree(env):
         smp.smp_serve_destroy(sv)
     for a, b in zip(alone[probe.idx], mixed[probe.idx]):
         assert torch.equal(a, b)
+    # the served job against the oracle on its stored BF16 values: BF16 sketch tolerance
+    _oracle_check(probe, A, B, mixed[probe.idx], 3e-3, 32768)
     # the same job through the plain pipeline (one context on torch's stream): the same bits again
     s = pipeline.Solver(probe.n, probe.n, probe.k, torch.bfloat16, seed=2 * probe.seed + 1, max_rows=32768)
     a = A[probe.row_offset:probe.row_offset + probe.d, :probe.n]
@@ -137,6 +156,8 @@ def test_batch_matches_single_instance(env):
     for got, key in zip(keep[probe.idx], ("U", "S", "V")):
         assert torch.equal(got, out[key])
     s.close()
+    # the batched instance against the oracle: the tuner's engine for FP32 inputs is the TF32 one (1e-3)
+    _oracle_check(probe, A32, B32, keep[probe.idx], 1e-3, 65536)
 
 
 def test_collect_timeout_and_destroy_with_live_jobs(env):

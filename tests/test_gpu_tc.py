@@ -89,23 +89,21 @@ def test_tc_philox_sketch_matches_oracle(env, same_ab):
     s.close()
 
 
-def test_tc_matches_simt_at_k500(env):
-    """The bench's sketch size k = 500 (two MMA boxes, 512 TMEM columns) on 4,000 rows, against the SIMT engine."""
+def test_tc_k500_matches_oracle(env):
+    """The bench's sketch size k = 500 (two MMA boxes, 512 TMEM columns) on one 4,000-row block with ragged column
+    tiles (n1 = 300, n2 = 260), against the oracle's binary64 sketch."""
     torch, smp, pipeline = env
     A, B = synth.lowrank_plus_noise(4000, 300, 260, 20, 0.1, 0.5, seed=5, dtype=np.float32)
-    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
-    out = {}
-    for name, eng in (("tc", smp.SMP_ENGINE_TC), ("simt", smp.SMP_ENGINE_SIMT)):
-        s = pipeline.Solver(300, 260, 500, torch.float32, seed=21, engine=eng, max_rows=4000)
-        s.sketch(Ad, Bd, 4000)
-        smp.smp_sync(s.ctx)
-        st = s.sketch_state()
-        out[name] = {k: st[k].cpu().numpy().astype(np.float64) for k in ("At", "Bt", "sA", "sB")}
-        s.close()
-    assert _colrel(out["tc"]["At"], out["simt"]["At"]) < 2e-3
-    assert _colrel(out["tc"]["Bt"], out["simt"]["Bt"]) < 2e-3
-    # two compensated FP32 sums with different chunking: each is within ~n 2^-48 of the exact sum
-    np.testing.assert_allclose(out["tc"]["sA"], out["simt"]["sA"], rtol=1e-12)
+    s = pipeline.Solver(300, 260, 500, torch.float32, seed=21, engine=smp.SMP_ENGINE_TC, max_rows=4000)
+    s.sketch(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), 4000)
+    smp.smp_sync(s.ctx)
+    st = s.sketch_state()
+    ref = O.sketch(A, B, 500, 21, block_rows=4000)
+    assert _colrel(st["At"].cpu().numpy().astype(np.float64), ref.At.T) < 2e-3
+    assert _colrel(st["Bt"].cpu().numpy().astype(np.float64), ref.Bt.T) < 2e-3
+    np.testing.assert_allclose(st["sA"].cpu().numpy(), ref.sA, rtol=1e-12)
+    np.testing.assert_allclose(st["sB"].cpu().numpy(), ref.sB, rtol=1e-12)
+    s.close()
 
 
 def test_tc_end_to_end_tiny(env):

@@ -92,22 +92,21 @@ def test_philox_sketch_matches_oracle(env, same_ab):
     s.close()
 
 
-def test_matches_tf32_engine_at_k500(env):
-    """The scale workload's k = 500 (two MMA boxes) on 4,000 rows (65,536-row contexts), against the TF32 engine."""
+def test_k500_matches_oracle(env):
+    """The scale workload's k = 500 (two MMA boxes) on one 4,000-row block with ragged column tiles, against the
+    oracle's binary64 sketch (BF16 rounding of both operands: 1e-2 per column)."""
     torch, smp, pipeline = env
     A, B = synth.lowrank_plus_noise(4000, 300, 260, 20, 0.1, 0.5, seed=5, dtype=np.float32)
-    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
-    out = {}
-    for name, eng in (("bf16", smp.SMP_ENGINE_TC_BF16), ("tf32", smp.SMP_ENGINE_TC)):
-        s = pipeline.Solver(300, 260, 500, torch.float32, seed=21, engine=eng)
-        s.sketch(Ad, Bd, 4000)
-        smp.smp_sync(s.ctx)
-        st = s.sketch_state()
-        out[name] = {k: st[k].cpu().numpy().astype(np.float64) for k in ("At", "Bt", "sA")}
-        s.close()
-    assert _colrel(out["bf16"]["At"], out["tf32"]["At"]) < 1e-2
-    assert _colrel(out["bf16"]["Bt"], out["tf32"]["Bt"]) < 1e-2
-    np.testing.assert_allclose(out["bf16"]["sA"], out["tf32"]["sA"], rtol=1e-12)
+    s = pipeline.Solver(300, 260, 500, torch.float32, seed=21, engine=smp.SMP_ENGINE_TC_BF16, max_rows=4000)
+    s.sketch(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), 4000)
+    smp.smp_sync(s.ctx)
+    st = s.sketch_state()
+    ref = O.sketch(A, B, 500, 21, block_rows=4000)
+    assert _colrel(st["At"].cpu().numpy().astype(np.float64), ref.At.T) < 1e-2
+    assert _colrel(st["Bt"].cpu().numpy().astype(np.float64), ref.Bt.T) < 1e-2
+    np.testing.assert_allclose(st["sA"].cpu().numpy(), ref.sA, rtol=1e-12)
+    np.testing.assert_allclose(st["sB"].cpu().numpy(), ref.sB, rtol=1e-12)
+    s.close()
 
 
 def test_end_to_end_tiny(env):
