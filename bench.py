@@ -8,7 +8,10 @@ sketch (16 blocks) + finalize + sample + estimate + WAltMin + canonical form.
 
 Prints one JSON line (rank 0). value = solves per second over all ranks (each rank solves its own instance:
 weak scaling, no data-path collective). `roofline` describes the sketch kernel (the dominant one), `e2e` the same
-metric with host-resident inputs copied in every step, `cpu_baseline` the CPU oracle on a bounded sample.
+metric through smp_sketch_accumulate_host with the inputs in pinned host memory, `cpu_baseline` and `oracle` the
+CPU oracle's whole solve of the same workload (its time, Omega bit for bit, its spectral error). On one GPU the
+line also carries the `precision`, `batched` and `serving` forms, each measured on its own workload outside the
+timed region with its own clocks and oracle comparison (--no-forms leaves them out).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--engine auto|simt|tc]
 """
@@ -152,6 +155,9 @@ def cpu_oracle_sample(w, seed_in, rows=CPU_SAMPLE_ROWS):
 
 
 def run_reference(args, w):
+    """The reference arm: the CPU oracle as it stands, on the machine's host cores. Each step is a bounded sample of the
+    workload (the single pass over CPU_SAMPLE_ROWS of the d rows plus sampling, estimate and WAltMin at full n);
+    `value` extrapolates the sample to a whole solve (the pass is linear in d) and says so."""
     world, rank, _ = dist_setup()
     if rank != 0:
         return
@@ -159,21 +165,50 @@ def run_reference(args, w):
     rows = CPU_SAMPLE_ROWS if args.workload == "scale" else w["d"]
     for _ in range(args.warmup):
         cpu_oracle_sample(w, 1001, rows)
-    per = []
+    per, walls = [], []
     for _ in range(args.steps):
-        p, _ = cpu_oracle_sample(w, 1001, rows)
+        p, wall = cpu_oracle_sample(w, 1001, rows)
         per.append(p)
+        walls.append(wall)
     value = len(per) / sum(per)
-    sample = ("single pass over %d of %d rows (time scaled by d/rows) + sampling, estimate, WAltMin at n=%d"
-              % (rows, w["d"], w["n1"]))
+    extrapolated = rows < w["d"]
+    sample = ("single pass over %d of %d rows + sampling, estimate, WAltMin at n = %d; solve time = pass time x "
+              "d / rows + the rest" % (rows, w["d"], w["n1"]))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(per) / len(per),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / len(walls),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "extrapolated": extrapolated,
+            "extrapolation": ("value = 1 / (sample pass time x %d / %d + sampling, estimate and WAltMin time); "
+                              "ms_per_step is the measured wall time of one sample step" % (w["d"], rows))
+            if extrapolated else None,
+            "extrapolated_ms_per_solve": 1e3 * sum(per) / len(per),
             "config": {"workload": args.workload, **{k: w[k] for k in ("d", "n1", "n2", "k", "r", "T")},
                        "block_rows": w["block"], "oracle": "CPU binary64 (numpy/LAPACK)"},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def OS_workers():
+    from tests import oracle_stream as OS
+    return OS.host_workers()
+
+
+def oracle_full_solve(w, fetch, m, same_ab=False):
+    """The CPU oracle's whole solve of a workload whose row blocks fetch(r0, r1) returns as host arrays: the single
+    pass with Pi's Philox blocks drawn by spawned worker processes (tests/oracle_stream.py schedules the oracle's own
+    functions), then sampling, estimate, WAltMin and the canonical form. Returns (result dict, wall seconds)."""
+    from tests import oracle_stream as OS
+    pool = OS.PiPool()
+    try:
+        t0 = time.perf_counter()
+        st = OS.sketch_stream(fetch, w["d"], w["n1"], w["n2"], w["k"], 1, w["block"], same_ab=same_ab, pool=pool)
+        ref = OS.solve_from_state(st, m, w["r"], w["T"], 2)
+        wall = time.perf_counter() - t0
+    finally:
+        pool.close()
+    ref["sA"], ref["sB"] = st.sA, st.sB
+    return ref, wall
 
 
 def spectral_error(torch, A, B, factors, block=65536):
@@ -194,6 +229,9 @@ def spectral_error(torch, A, B, factors, block=65536):
 
 
 def main():
+    # the batched and serving forms run many jobs on streams of their own: let more of them reach the device at once
+    # (process-local; it must be set before the CUDA context exists)
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -211,6 +249,8 @@ def main():
     ap.add_argument("--size", type=int, default=0, help="table1 workload: d = n = SIZE instead of 100,000")
     ap.add_argument("--no-baseline", action="store_true",
                     help="skip the SVD(A~^T B~) and multinomial-sampling comparisons")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="scale workload: leave the precision / batched / serving sub-objects out of the line")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -224,6 +264,7 @@ def main():
     if args.workload == "table1":
         return run_table1(args, w)
 
+    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -315,6 +356,10 @@ def main():
         dist.barrier()
     launches = smp.smp_launch_count() - launches0
     clk = clocks.stop()
+    om_last = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:   # the last timed solve's Omega, for the oracle leg
+        om_last = {key: (v.cpu().numpy() if hasattr(v, "cpu") else v)
+                   for key, v in solvers[(args.steps - 1) % 2].omega().items()}
     elapsed = t_start.elapsed_time(t_end) / 1e3
     if world > 1:
         elapsed = max_over_ranks(elapsed, dist, dev)
@@ -472,16 +517,38 @@ def main():
                 "exact_useful_tflops": 2.0 * nnz_l * x_rows / x_avg / 1e12, "spectral_err": None}
         ls.close()
 
+    # the CPU oracle's whole solve of the same workload (same bytes, same seeds): the CPU baseline (timed, every row,
+    # no extrapolation) and the parity of the timed solve (Omega bit for bit, spectral error)
+    ref, cpu, orc = None, None, None
+    if om_last is not None:
+        ref, o_wall = oracle_full_solve(w, lambda r0, r1: (A[r0:r1].cpu().numpy(), B[r0:r1].cpu().numpy()), m)
+        rows_gpu = np.repeat(np.arange(w["n1"]), np.diff(om_last["row_ptr"]))
+        omega_equal = bool(om_last["nnz"] == ref["rows"].shape[0] and np.array_equal(om_last["col"], ref["cols"])
+                           and np.array_equal(rows_gpu, ref["rows"]))
+        workers = OS_workers()
+        cpu = {"value": 1.0 / o_wall, "unit": "solves/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+               "sample": "one whole solve of the workload (all %d rows, no extrapolation): the oracle's single pass "
+                         "with its Pi blocks drawn by %d spawned processes and its products on the main process's "
+                         "BLAS, then sampling, estimate, WAltMin and the canonical form; %.1f s"
+                         % (w["d"], workers, o_wall)}
+        orc = {"omega_equal": omega_equal, "nnz": int(ref["rows"].shape[0]), "spectral_err": None,
+               "err_diff": None, "tolerance": 1e-3, "wall_s": o_wall}
+
     err, opt_err = None, None
     if not args.no_error and rank == 0:
         extra = ([(Ub, Sb, Vb)] if base else []) + ([(Um, Sm, Vm)] if mn else []) + ([(Ul, Sl, Vl)] if lela else []) \
             + ([(Ua, Sa, Va)] if alt else [])
+        if ref is not None:
+            extra.append(tuple(torch.from_numpy(np.ascontiguousarray(ref[x])).to(dev) for x in ("U", "S", "V")))
         errs, opt_err = spectral_error(torch, A, B, [(U, S, V)] + extra)
         err = errs[0]
         rest = errs[1:]
         for entry in (base, mn, lela, alt):
             if entry:
                 entry["spectral_err"] = rest.pop(0)
+        if orc is not None:
+            orc["spectral_err"] = rest.pop(0)
+            orc["err_diff"] = abs(err - orc["spectral_err"])
 
     # ---- end to end: host-resident inputs copied in every step (pinned, double-buffered row blocks)
     e2e = None
@@ -489,13 +556,6 @@ def main():
         with torch.cuda.stream(streams[0]):
             e2e = run_e2e(torch, smp, solver, A, B, w, m, rank, args.e2e_steps, streams[0], world, dev)
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rows = CPU_SAMPLE_ROWS if args.workload == "scale" else w["d"]
-        per, wall = cpu_oracle_sample(w, 1001, rows)
-        cpu = {"value": 1.0 / per, "unit": "solves/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-               "sample": "single pass over %d of %d rows (time x d/rows) + sampling, estimate and WAltMin at "
-                         "n = %d; %.1f s of CPU wall time" % (rows, w["d"], w["n1"], wall)}
 
     in_gb = w["d"] * (w["n1"] + w["n2"]) * 4 / 1e9
     l2_note = ("inputs (%.1f GB) larger than L2; no flush" % in_gb) if in_gb > 0.129 else "inputs fit in L2"
@@ -512,15 +572,27 @@ def main():
                 "p50_ms": statistics.median(step_ms), "p99_ms": step_ms[min(len(step_ms) - 1,
                                                                             int(math.ceil(0.99 * len(step_ms))) - 1)],
                 "sketch_gbs": roof["hbm_gbs"], "spectral_err": err, "optimal_err": opt_err,
+                "oracle_err": orc["spectral_err"] if orc else None,
+                "omega_equal": orc["omega_equal"] if orc else None, "oracle": orc,
                 "baseline_sketch_svd": base, "sampler_multinomial": mn, "lela": lela, "engine_bf16_operands": alt,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk}
+    for sv in solvers:
+        sv.close()
+    if rank == 0 and world == 1 and args.workload == "scale" and not args.no_forms:
+        # the three forms of the method on their own workloads, each outside the timed region above and with its
+        # own clocks, launch count and oracle comparison: precision (BF16 / FP8 / FP32 sketches), batched (256
+        # uneven instances), serving (Poisson arrivals)
+        del A, B
+        torch.cuda.empty_cache()
+        line["precision"] = run_precision(args, WORKLOADS["precision"], embed=True)
+        line["batched"] = run_batched(args, WORKLOADS["batch"], embed=True)
+        line["serving"] = run_serving(args, WORKLOADS["serve"], embed=True)
+    if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
-    for sv in solvers:
-        sv.close()
 
 
 def implicit_errors(torch, A, factors, r, iters=40, block=16, seed=0):
@@ -601,9 +673,31 @@ def run_table1(args, w):
     print(json.dumps(line), flush=True)
 
 
-def run_serving(args, w):
+def oracle_job_check(torch, spec, pool_A, pool_B, factors, block_rows, tol):
+    """One job / instance of the serving or batched form against the CPU oracle run on its window of the pool (the
+    stored values, the job's seeds): spectral errors of both against the same A^T B and the size of Omega."""
+    import numpy as np
+    from oracle import smp as O
+    a = pool_A[spec.row_offset:spec.row_offset + spec.d, :spec.n]
+    b = pool_B[spec.row_offset:spec.row_offset + spec.d, :spec.n]
+    a64 = a.float().cpu().numpy().astype(np.float64)
+    b64 = b.float().cpu().numpy().astype(np.float64)
+    t0 = time.perf_counter()
+    ref = O.smp_pca(a64, b64, spec.r, spec.k, spec.m, spec.T, seed=2 * spec.seed + 1, sample_seed=2 * spec.seed + 2,
+                    block_rows=block_rows)
+    wall = time.perf_counter() - t0
+    dev = pool_A.device
+    fac = [factors, tuple(torch.from_numpy(np.ascontiguousarray(ref[x])).to(dev) for x in ("U", "S", "V"))]
+    (e_gpu, e_ref), opt = spectral_error(torch, a, b, fac)
+    return {"job": {"n": spec.n, "d": spec.d, "r": spec.r, "k": spec.k}, "spectral_err": e_gpu, "oracle_err": e_ref,
+            "err_diff": abs(e_gpu - e_ref), "tolerance": tol, "optimal_err": opt, "oracle_nnz": int(ref["rows"].shape[0]),
+            "oracle_wall_s": wall}
+
+
+def run_serving(args, w, embed=False):
     """The serving form (one GPU): Poisson job arrivals at w["rate"] per second through libsmp's server; reports
-    completed solves per second over the run and the latency from each job's last block to its factors."""
+    completed solves per second over the run and the latency from each job's last block to its factors. One job is
+    also solved by the CPU oracle on its window of the pool and compared."""
     # many jobs run on streams of their own: let more of them reach the device concurrently (process-local)
     os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     import torch
@@ -625,10 +719,14 @@ def run_serving(args, w):
         warm = serve.poisson_jobs(w["warm_jobs"], w["rate"], seed=99, pool_rows=w["pool_rows"], T=w["T"])
         serve.run(server, warm, pool_A, pool_B, sdt, block_rows=w["block"])
         jobs = serve.poisson_jobs(w["jobs"], w["rate"], seed=5, pool_rows=w["pool_rows"], T=w["T"])
+        probe = min(jobs[:50], key=lambda j: j.d * j.n)          # a small early job, for the oracle comparison
+        keep = {probe.idx: (torch.empty(probe.n, probe.r, dtype=torch.float64, device="cuda"),
+                            torch.empty(probe.r, dtype=torch.float64, device="cuda"),
+                            torch.empty(probe.n, probe.r, dtype=torch.float64, device="cuda"))}
         clocks = ClockSampler(0)
         clocks.start()
         launches0 = smp.smp_launch_count()
-        records, wall = serve.run(server, jobs, pool_A, pool_B, sdt, block_rows=w["block"])
+        records, wall = serve.run(server, jobs, pool_A, pool_B, sdt, block_rows=w["block"], keep=keep)
         launches = smp.smp_launch_count() - launches0
         clk = clocks.stop()
     finally:
@@ -649,12 +747,22 @@ def run_serving(args, w):
             "mean_latency_ms": sum(lat) / len(lat), "wall_s": wall, "input_gb_streamed": streamed / 1e9,
             "input_gbs": streamed / wall / 1e9, "gpu_launches": int(launches), "clocks": clk,
             "roofline": None, "cpu_baseline": None, "e2e": None}
+    if not args.no_cpu_baseline:
+        line["oracle"] = oracle_job_check(torch, probe, pool_A, pool_B, keep[probe.idx], w["block"],
+                                          1e-3 if f32 else 3e-3)
+    del pool_A, pool_B
+    torch.cuda.empty_cache()
+    if embed:
+        return line
     print(json.dumps(line), flush=True)
 
 
-def run_precision(args, w):
+def run_precision(args, w, embed=False):
     """The precision form (one GPU): solves/s and spectral error of SMP-PCA with the sketch in BF16, in FP8 E4M3
-    (tensor cores) and in FP32 (CUDA cores) on the same BF16-stored inputs; WAltMin's solves in binary64."""
+    (tensor cores) and in FP32 (CUDA cores) on the same BF16-stored inputs; WAltMin's solves in binary64. Then the
+    BF16 and FP8 paths and the CPU oracle on the d = 200,000 row prefix of the same inputs: Omega and the spectral
+    errors compared."""
+    import numpy as np
     import torch
     from paper_1610_06656_gb300 import build, pipeline, smp, synth
     smp.load(build.build())
@@ -665,11 +773,16 @@ def run_precision(args, w):
     m = pipeline.default_m(w["n1"], w["n2"], w["r"])
     stream = torch.cuda.current_stream()
     results = {}
-    peaks, _ = measured_peaks()
-    forms = (("bf16", torch.bfloat16, smp.SMP_ENGINE_TC), ("fp8_e4m3", torch.bfloat16, smp.SMP_ENGINE_TC_FP8),
-             ("fp32", torch.float32, smp.SMP_ENGINE_SIMT))
+    peaks, peak_kind = measured_peaks()
+    # (name, stored dtype, engine, timed solves): the FP32 CUDA-core path takes ~2.3 s a solve, so it is timed on 2
+    forms = (("bf16", torch.bfloat16, smp.SMP_ENGINE_TC, w["steps"]),
+             ("fp8_e4m3", torch.bfloat16, smp.SMP_ENGINE_TC_FP8, w["steps"]),
+             ("fp32", torch.float32, smp.SMP_ENGINE_SIMT, min(2, w["steps"])))
     factors = []
-    for name, tdt, eng in forms:
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = smp.smp_launch_count()
+    for name, tdt, eng, steps in forms:
         Xa, Xb = (A, B) if tdt == torch.bfloat16 else (A.float(), B.float())
         # two contexts on two streams, consecutive solves alternating: solve i + 1's sketch runs while solve i's
         # WAltMin finishes (as in the scale bench)
@@ -708,7 +821,7 @@ def run_precision(args, w):
         t0.record(stream)
         for st in sts:
             st.wait_event(t0)
-        (U, S, V), nnz = run(w["steps"])
+        (U, S, V), nnz = run(steps)
         for st in sts:
             ev = torch.cuda.Event()
             ev.record(st)
@@ -716,36 +829,75 @@ def run_precision(args, w):
         t1.record(stream)
         torch.cuda.synchronize()
         sk_ms = [a.elapsed_time(b) for a, b in sk_ev]
-        ms = t0.elapsed_time(t1) / w["steps"]
-        in_bytes = w["d"] * (w["n1"] + w["n2"]) * (2 if tdt == torch.bfloat16 else 4)
+        ms = t0.elapsed_time(t1) / steps
+        in_bytes = w["d"] * (w["n1"] + w["n2"]) * 2
         flops = 2.0 * w["k"] * w["d"] * (w["n1"] + w["n2"])
-        results[name] = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms, "sketch_ms": sum(sk_ms) / len(sk_ms),
-                         "sketch_tflops": flops / (sum(sk_ms) / len(sk_ms)) / 1e9,
-                         "sketch_gbs": in_bytes / (sum(sk_ms) / len(sk_ms)) / 1e6, "nnz": int(nnz)}
+        sk_s = sum(sk_ms) / len(sk_ms) / 1e3
+        results[name] = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms, "timed_solves": steps,
+                         "sketch_ms": sk_s * 1e3, "sketch_tflops": flops / sk_s / 1e12,
+                         "sketch_gbs": in_bytes / sk_s / 1e9, "nnz": int(nnz)}
         factors.append((U.clone(), S.clone(), V.clone()))
         for sv in svs:
             sv.close()
         del Xa, Xb
         torch.cuda.empty_cache()
+    launches = smp.smp_launch_count() - launches0
+    clk = clocks.stop()
+    bf = results["bf16"]
+    roof = {"bound": "tensor", "achieved": bf["sketch_tflops"], "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+            "frac": bf["sketch_tflops"] / peaks["bf16_tflops"], "traffic": None,
+            "peak_kind": "%s bf16 burst" % peak_kind,
+            "kernel": "BF16 sketch of a whole solve (sketch_bf16_kernel + pi_gen_kernel, 62 blocks), CUDA events "
+                      "around the 62 smp_sketch_accumulate calls",
+            "hbm_frac": bf["sketch_gbs"] / peaks["hbm_gbs"]}
     opt = None
     if not args.no_error:
         errs, opt = spectral_error(torch, A, B, factors)
-        for (name, _, _), e in zip(forms, errs):
+        for (name, _, _, _), e in zip(forms, errs):
             results[name]["spectral_err"] = e
+    prefix = None
+    if not args.no_cpu_baseline:
+        d0 = 200_000
+        Ap, Bp = A[:d0], B[:d0]
+        res, fac = {}, []
+        for name, eng in (("bf16", smp.SMP_ENGINE_TC), ("fp8_e4m3", smp.SMP_ENGINE_TC_FP8)):
+            sv = pipeline.Solver(w["n1"], w["n2"], w["k"], torch.bfloat16, seed=1, engine=eng, max_rows=w["block"])
+            out = sv.solve(Ap, Bp, w["r"], w["T"], m=m, sample_seed=2, walt_seed=3, block_rows=w["block"])
+            torch.cuda.synchronize()
+            om = {key: (v.cpu().numpy() if hasattr(v, "cpu") else v) for key, v in sv.omega().items()}
+            sv.close()
+            res[name] = om
+            fac.append((out["U"], out["S"], out["V"]))
+        ref, o_wall = oracle_full_solve(dict(w, d=d0), lambda r0, r1: (Ap[r0:r1].float().cpu().numpy(),
+                                                                       Bp[r0:r1].float().cpu().numpy()), m)
+        fac.append(tuple(torch.from_numpy(np.ascontiguousarray(ref[x])).to(A.device) for x in ("U", "S", "V")))
+        errs, popt = spectral_error(torch, Ap, Bp, fac)
+        prefix = {"d": d0, "oracle_err": errs[2], "optimal_err": popt, "oracle_wall_s": o_wall,
+                  "oracle_nnz": int(ref["rows"].shape[0])}
+        for (name, om), e, tol in zip(res.items(), errs[:2], (3e-3, 1e-2)):
+            rows_gpu = np.repeat(np.arange(w["n1"]), np.diff(om["row_ptr"]))
+            prefix[name] = {"spectral_err": e, "err_diff": abs(e - errs[2]), "tolerance": tol,
+                            "omega_equal": bool(om["nnz"] == ref["rows"].shape[0] and
+                                                np.array_equal(om["col"], ref["cols"]) and
+                                                np.array_equal(rows_gpu, ref["rows"]))}
     line = {"metric": "precision form: solves/s and spectral error per sketch precision (same BF16-stored inputs)",
             "value": results["bf16"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": w["steps"],
             "warmup": w["warm"], "ms_per_step": results["bf16"]["ms_per_solve"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
             "data": "synthetic (low rank 32 + noise 0.05, column scales (j+1)^-0.7), stored in BF16",
-            "config": {"workload": args.workload, **{k: w[k] for k in ("d", "n1", "n2", "k", "r", "T")},
+            "config": {"workload": "precision", **{k: w[k] for k in ("d", "n1", "n2", "k", "r", "T")},
                        "block_rows": w["block"], "m": m,
                        "l2": "inputs (%.1f GB) larger than L2; no flush" % (w["d"] * (w["n1"] + w["n2"]) * 2 / 1e9)},
-            "forms": results, "optimal_err": opt, "bf16_peak_tflops": peaks["bf16_tflops"],
-            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None}
+            "forms": results, "optimal_err": opt, "oracle_prefix": prefix, "bf16_peak_tflops": peaks["bf16_tflops"],
+            "roofline": roof, "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clk}
+    del A, B
+    torch.cuda.empty_cache()
+    if embed:
+        return line
     print(json.dumps(line), flush=True)
 
 
-def run_batched(args, w):
+def run_batched(args, w, embed=False):
     """The batched form (one GPU): w["instances"] independent FP32 instances solved together through libsmp's
     server, each instance's sketch engine chosen by the autotuner; reports instances solved per second and the
     input bandwidth the whole batch sustained."""
@@ -773,10 +925,14 @@ def run_batched(args, w):
     try:
         batch.run(server, batch.instances(w["warm"], seed=98, pool_rows=w["pool_rows"], T=w["T"]), pool_A, pool_B,
                   sdt, tuner, block_rows=w["block"])
+        probe = min(specs[:50], key=lambda j: j.d * j.n)        # a small instance, for the oracle comparison
+        keep = {probe.idx: (torch.empty(probe.n, probe.r, dtype=torch.float64, device="cuda"),
+                            torch.empty(probe.r, dtype=torch.float64, device="cuda"),
+                            torch.empty(probe.n, probe.r, dtype=torch.float64, device="cuda"))}
         clocks = ClockSampler(0)
         clocks.start()
         launches0 = smp.smp_launch_count()
-        records, wall = batch.run(server, specs, pool_A, pool_B, sdt, tuner, block_rows=w["block"])
+        records, wall = batch.run(server, specs, pool_A, pool_B, sdt, tuner, block_rows=w["block"], keep=keep)
         launches = smp.smp_launch_count() - launches0
         clk = clocks.stop()
     finally:
@@ -803,6 +959,13 @@ def run_batched(args, w):
             "hbm_frac": streamed / wall / 1e9 / peaks["hbm_gbs"], "hbm_peak_kind": peak_kind,
             "p50_ms": statistics.median(lat), "p99_ms": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
             "gpu_launches": int(launches), "clocks": clk, "roofline": None, "cpu_baseline": None, "e2e": None}
+    if not args.no_cpu_baseline:
+        line["oracle"] = oracle_job_check(torch, probe, pool_A, pool_B, keep[probe.idx], w["block"],
+                                          3e-3 if bf16 else 1e-3)
+    del pool_A, pool_B
+    torch.cuda.empty_cache()
+    if embed:
+        return line
     print(json.dumps(line), flush=True)
 
 
@@ -829,36 +992,25 @@ def tc_active(smp):
 
 
 def run_e2e(torch, smp, solver, A, B, w, m, rank, steps, stream, world, dev):
-    """Same solve with A, B in pinned host memory: every step copies each 65,536-row block host->device (on a copy
-    stream, two device buffers in flight) before it is sketched, and reads U, S, V back."""
+    """The same solve through the C ABI with the inputs in pinned HOST memory: every step hands each 65,536-row
+    block to smp_sketch_accumulate_host (the library copies it into one of its two device staging buffers on its
+    copy stream while the previous block is sketched) and reads U, S, V back to pinned host memory. Also reports the
+    effective host-to-device rate and this box's pinned copy rate measured alone, so the e2e time can be read as
+    input bytes / link rate."""
     blk = w["block"]
     Ah = torch.empty(A.shape, dtype=A.dtype, pin_memory=True)
     Bh = torch.empty(B.shape, dtype=B.dtype, pin_memory=True)
     Ah.copy_(A)
     Bh.copy_(B)
-    bufA = [torch.empty(blk, w["n1"], dtype=A.dtype, device=dev) for _ in range(2)]
-    bufB = [torch.empty(blk, w["n2"], dtype=B.dtype, device=dev) for _ in range(2)]
-    copy_stream = torch.cuda.Stream(device=dev)
-    copied = [torch.cuda.Event() for _ in range(2)]
-    consumed = [torch.cuda.Event() for _ in range(2)]
     outU = torch.empty(w["n1"], w["r"], dtype=torch.float64, pin_memory=True)
     outS = torch.empty(w["r"], dtype=torch.float64, pin_memory=True)
     outV = torch.empty(w["n2"], w["r"], dtype=torch.float64, pin_memory=True)
 
     def one():
         smp.smp_sketch_reset(solver.ctx)
-        starts = list(range(0, w["d"], blk))
-        for idx, r0 in enumerate(starts):
+        for r0 in range(0, w["d"], blk):
             r1 = min(w["d"], r0 + blk)
-            s = idx & 1
-            with torch.cuda.stream(copy_stream):
-                copy_stream.wait_event(consumed[s])
-                bufA[s][:r1 - r0].copy_(Ah[r0:r1], non_blocking=True)
-                bufB[s][:r1 - r0].copy_(Bh[r0:r1], non_blocking=True)
-                copied[s].record(copy_stream)
-            stream.wait_event(copied[s])
-            smp.smp_sketch_accumulate(solver.ctx, bufA[s], w["n1"], bufB[s], w["n2"], r0, r1 - r0)
-            consumed[s].record(stream)
+            smp.smp_sketch_accumulate_host(solver.ctx, Ah[r0:r1], w["n1"], Bh[r0:r1], w["n2"], r0, r1 - r0)
         smp.smp_sketch_finalize(solver.ctx)
         nnz = solver.sample(m, 2 + rank)
         vals = solver.estimate(nnz)
@@ -868,8 +1020,6 @@ def run_e2e(torch, smp, solver, A, B, w, m, rank, steps, stream, world, dev):
         outV.copy_(V, non_blocking=True)
         stream.synchronize()
 
-    for ev in consumed:
-        ev.record(stream)
     one()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -882,8 +1032,25 @@ def run_e2e(torch, smp, solver, A, B, w, m, rank, steps, stream, world, dev):
         el = max_over_ranks(el, dist, dev)
     h2d = (A.numel() * A.element_size() + B.numel() * B.element_size())
     d2h = (outU.numel() + outS.numel() + outV.numel()) * 8
+    # the link alone: one pinned block pair copied host-to-device, CUDA events on a copy stream
+    cs = torch.cuda.Stream(device=dev)
+    dA = torch.empty(blk, w["n1"], dtype=A.dtype, device=dev)
+    dB = torch.empty(blk, w["n2"], dtype=B.dtype, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(cs):
+        dA.copy_(Ah[:blk], non_blocking=True)
+        e0.record(cs)
+        for _ in range(4):
+            dA.copy_(Ah[:blk], non_blocking=True)
+            dB.copy_(Bh[:blk], non_blocking=True)
+        e1.record(cs)
+    cs.synchronize()
+    link = 4 * (dA.numel() + dB.numel()) * A.element_size() / (e0.elapsed_time(e1) / 1e3) / 1e9
+    del Ah, Bh, dA, dB
     return {"value": world * steps / el, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "ms_per_step": 1e3 * el / steps}
+            "ms_per_step": 1e3 * el / steps, "api": "smp_sketch_accumulate_host (pinned host blocks)",
+            "h2d_gbs_effective": h2d / (el / steps) / 1e9, "h2d_link_gbs_measured": link,
+            "bound_ms_by_link": 1e3 * h2d / (link * 1e9)}
 
 
 if __name__ == "__main__":

@@ -15,8 +15,10 @@
 //     column sums, round x to TF32 (cvt.rna) and write it back K-major (64-byte swizzle, conflict-free 16-byte
 //     stores). Warp 1 (one thread) issues tcgen05.mma kind::tf32 with M = 128 data columns and N = 256 sketch
 //     rows per instruction into a TMEM accumulator of 128 lanes x up to 512 columns. Warps 4-7 then drain TMEM
-//     with tcgen05.ld and add the tile into the split's partial sketch. Every wait is bounded (%globaltimer); a
-//     timeout sets the device error word and the CTA unwinds.
+//     with tcgen05.ld and add the tile into the split's partial sketch. Every wait is bounded (%globaltimer, the
+//     limit a kernel argument): a timeout sets the device error word and raises the CTA's abort flag; every role
+//     leaves its loop, the producers wait (bounded) until the loads they issued have landed, the MMA warp commits
+//     the accumulator barrier anyway so the MMAs in flight are waited for, the drain is skipped and TMEM is freed.
 #include <cuda.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
@@ -154,6 +156,8 @@ struct TcArgs {
     float* part;            // [splits][ntot][ldk]
     double* nsq;            // [splits][ntot]
     int* err;
+    unsigned long long wait_ns;   // limit of every mbarrier wait
+    int skip_stage;               // test hook: the data producer issues nothing from this stage on (-1: never)
 };
 
 template <bool B16>
@@ -230,11 +234,14 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
     if (warp == 0) {
         // ---------------- data producer: column-major data tiles into the staging ring (lane 0 issues)
         if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)tm_data) : "memory");
+        int issued = 0;
         for (int it = 0; it < n_it; ++it) {
+            if (it == args.skip_stage) break;   // test hook: the loads of this stage never come
             const int d = it % DSTAGES;
             const uint32_t ph = (uint32_t)(it / DSTAGES) & 1u;
             bool ok = true;
-            if (it >= DSTAGES) ok = __all_sync(0xffffffffu, mbar_wait(dempty_bar(d), ph ^ 1u, abort_flag));
+            if (it >= DSTAGES)
+                ok = __all_sync(0xffffffffu, mbar_wait_for(dempty_bar(d), ph ^ 1u, abort_flag, args.wait_ns));
             if (!ok) {
                 if (lane == 0) {
                     *abort_flag = 1;
@@ -253,6 +260,7 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
                         tma_load_2d(dst + g * KGROUP_BYTES + b * DATA_BOX_BYTES, tm_data, (int)col0 + 32 * b,
                                     t + 8 * g, dfull_bar(d));
             }
+            issued = it + 1;
             __syncwarp();
         }
         // the TMEM drain reads and rewrites this tile's slice of the split's partial sketch: bring it into L2 while
@@ -265,15 +273,20 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(pr));
             }
         }
+        // the CTA may not finish while a load it issued is still landing in its shared memory
+        for (int it = max(0, issued - DSTAGES); it < issued; ++it)
+            mbar_wait_for(dfull_bar(it % DSTAGES), (uint32_t)(it / DSTAGES) & 1u, abort_flag, args.wait_ns);
     } else if (warp == 2) {
         // ---------------- Pi producer: Pi tiles into the main ring once the MMA has released the stage
         if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_pi) : "memory");
         const uint32_t bytes = args.nh * PI_BOX_BYTES;
+        int issued = 0;
         for (int it = 0; it < n_it; ++it) {
             const int s = it % PSTAGES;
             const uint32_t ph = (uint32_t)(it / PSTAGES) & 1u;
             bool ok = true;
-            if (it >= PSTAGES) ok = __all_sync(0xffffffffu, mbar_wait(pempty_bar(s), ph ^ 1u, abort_flag));
+            if (it >= PSTAGES)
+                ok = __all_sync(0xffffffffu, mbar_wait_for(pempty_bar(s), ph ^ 1u, abort_flag, args.wait_ns));
             if (!ok) {
                 if (lane == 0) {
                     *abort_flag = 1;
@@ -288,8 +301,11 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
                     tma_load_2d(pring + s * PI_STAGE_BYTES + h * PI_BOX_BYTES, &tm_pi, t, h * PI_BOX_ROWS,
                                 pfull_bar(s));
             }
+            issued = it + 1;
             __syncwarp();
         }
+        for (int it = max(0, issued - PSTAGES); it < issued; ++it)
+            mbar_wait_for(pfull_bar(it % PSTAGES), (uint32_t)(it / PSTAGES) & 1u, abort_flag, args.wait_ns);
     } else if (warp == 1) {
         // ---------------- MMA issuer (the whole warp waits; lane 0 issues)
         const uint32_t id_full = B16 ? idesc_bf16(TILE_M, PI_BOX_ROWS, false) : idesc_tf32(TILE_M, PI_BOX_ROWS);
@@ -298,8 +314,8 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
         for (int it = 0; it < n_it; ++it) {
             const int sp = it % PSTAGES, sa = it % ASTAGES;
             const uint32_t pph = (uint32_t)(it / PSTAGES) & 1u, aph = (uint32_t)(it / ASTAGES) & 1u;
-            ok = __all_sync(0xffffffffu,
-                            mbar_wait(pfull_bar(sp), pph, abort_flag) && mbar_wait(afull_bar(sa), aph, abort_flag));
+            ok = __all_sync(0xffffffffu, mbar_wait_for(pfull_bar(sp), pph, abort_flag, args.wait_ns) &&
+                                             mbar_wait_for(afull_bar(sa), aph, abort_flag, args.wait_ns));
             if (!ok) {
                 if (lane == 0) {
                     *abort_flag = 1;
@@ -330,7 +346,8 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
             }
             __syncwarp();
         }
-        if (ok && lane == 0) mma_commit(acc_bar);
+        // always: the accumulator commit also tells the drain when the MMAs in flight have finished
+        if (lane == 0) mma_commit(acc_bar);
         __syncwarp();
     } else if (copy_index(warp) >= 0) {
         // ---------------- copy warps: a 32-column box and the 8-row groups ci / 4 (+ 2) of the stage: column sums of
@@ -344,8 +361,8 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
             const uint32_t dph = (uint32_t)(it / DSTAGES) & 1u;
             const int s = it % ASTAGES;
             const uint32_t ph = (uint32_t)(it / ASTAGES) & 1u;
-            bool ok = mbar_wait(dfull_bar(d), dph, abort_flag);
-            if (ok && it >= ASTAGES) ok = mbar_wait(aempty_bar(s), ph ^ 1u, abort_flag);   // copy slot free
+            bool ok = mbar_wait_for(dfull_bar(d), dph, abort_flag, args.wait_ns);
+            if (ok && it >= ASTAGES) ok = mbar_wait_for(aempty_bar(s), ph ^ 1u, abort_flag, args.wait_ns);   // slot free
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) {
                 if (lane == 0) {
@@ -410,7 +427,8 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
         const int m = q * 32 + lane;
         const int cq = ((args.kc / 32 + 3) / 4) * 32;   // accumulator columns per warp (multiple of 32)
         const int cbeg = (warp >> 2) * cq, cend = min(args.kc, cbeg + cq);
-        const bool acc_ok = __all_sync(0xffffffffu, !*abort_flag && mbar_wait(acc_bar, 0, abort_flag));
+        const bool landed = __all_sync(0xffffffffu, mbar_wait_for(acc_bar, 0, abort_flag, args.wait_ns));
+        const bool acc_ok = landed && !*abort_flag;
         if (acc_ok) {
             tc_fence_after();
             const int64_t c = cbase + m;
@@ -439,7 +457,7 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
                 }
             }
             if (warp < 4 && m < valid) args.nsq[(int64_t)split * args.ntot + c] += nsum[m] + nsum[TILE_M + m];
-        } else if (lane == 0) {
+        } else if (!landed && lane == 0) {
             *abort_flag = 1;
             set_error(args.err, DEVERR_TIMEOUT | (1 << 11));
         }
@@ -696,6 +714,9 @@ cudaError_t launch_sketch_tc_pi(smp_ctx* c, const void* A, int64_t lda, const vo
     a.part = (float*)c->part;
     a.nsq = c->nsq;
     a.err = c->dev_err;
+    const int64_t wait = g_tc_wait_ns.load(std::memory_order_relaxed);
+    a.wait_ns = wait > 0 ? (unsigned long long)wait : WAIT_NS;
+    a.skip_stage = g_tc_skip_stage.exchange(-1, std::memory_order_relaxed);
     const dim3 grid = smp::counted(dim3((unsigned)tiles, (unsigned)splits));
     if (b16) sketch_tc_kernel<true><<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, mp, a);
     else sketch_tc_kernel<false><<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, mp, a);

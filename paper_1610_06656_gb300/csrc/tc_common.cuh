@@ -73,6 +73,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
 }
 
+// The same wait with the limit given at run time (the tensor-core sketch takes it as a kernel argument).
+__device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                              unsigned long long limit_ns) {
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = global_timer();
+    for (;;) {
+        if (mbar_test(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (global_timer() - t0 > limit_ns) return false;
+    }
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
