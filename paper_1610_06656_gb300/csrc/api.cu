@@ -357,13 +357,17 @@ smp_status smp_sketch_accumulate_host(smp_ctx* c, const void* A, int64_t lda, co
     const int b = c->host_next;
     char* dA = (char*)c->host_stage[b];
     char* dB = dA + (size_t)c->max_rows * pitch_a * esz;
+    // a block whose rows are already packed at the staging pitch goes in one linear copy (a 2-D copy of 65,536
+    // short rows costs the copy engine per row and ran at a quarter of the link's rate)
+    auto copy_rows = [&](void* dst, int64_t dpitch, const void* src, int64_t spitch, int64_t width) {
+        if (spitch == dpitch && width == dpitch)
+            return cudaMemcpyAsync(dst, src, (size_t)nrows * dpitch * esz, cudaMemcpyHostToDevice, c->copy_stream);
+        return cudaMemcpy2DAsync(dst, dpitch * esz, src, spitch * esz, width * esz, nrows, cudaMemcpyHostToDevice,
+                                 c->copy_stream);
+    };
     e = cudaStreamWaitEvent(c->copy_stream, c->host_consumed[b], 0);   // the sketch that last read buffer b ended
-    if (e == cudaSuccess)
-        e = cudaMemcpy2DAsync(dA, pitch_a * esz, A, lda * esz, c->p.n1 * esz, nrows, cudaMemcpyHostToDevice,
-                              c->copy_stream);
-    if (e == cudaSuccess && !c->p.same_ab)
-        e = cudaMemcpy2DAsync(dB, pitch_b * esz, B, ldb * esz, c->p.n2 * esz, nrows, cudaMemcpyHostToDevice,
-                              c->copy_stream);
+    if (e == cudaSuccess) e = copy_rows(dA, pitch_a, A, lda, c->p.n1);
+    if (e == cudaSuccess && !c->p.same_ab) e = copy_rows(dB, pitch_b, B, ldb, c->p.n2);
     if (e == cudaSuccess) e = cudaEventRecord(c->host_copied[b], c->copy_stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->host_copied[b], 0);
     if (e != cudaSuccess) return check_cuda(c, e, "smp_sketch_accumulate_host: host-to-device copy");

@@ -6,11 +6,11 @@
 //  1. pi_gen_kernel writes Pi[a][t] (t contiguous, rounded to TF32) for the block's rows into a context buffer.
 //     Generating Pi once per block and letting every column tile read it (through L2) costs one Gaussian per
 //     (sketch row, data row); regenerating it inside each column tile would cost (n1 + n2) / 128 times more.
-//  2. sketch_tc_kernel: one CTA per (128-column tile, row split). Warp 0 issues TMA loads of the data tile (rows
-//     of A are contiguous along the columns, so the tile lands column-major for the MMA: 32-column x 8-row
-//     boxes, 128-byte swizzle) into an 8-slot staging ring; warp 2 issues TMA loads of the Pi tile (K-major,
-//     64-byte swizzle, 256-row boxes) into a 4-slot ring, all guarded by mbarriers (the deeper data ring keeps
-//     more HBM reads in flight). kind::tf32 takes K-major operands only, so warps 4-7 (one
+//  2. sketch_tc_kernel: one CTA per (128-column tile, row split; the splits interleaved by pipeline stage). Warp 0
+//     issues one TMA load per stage of the data tile (rows of A are contiguous along the columns, so the tile lands
+//     column-major: one 128-column x KS-row box, no swizzle) into an 8-slot staging ring; warp 2 issues TMA loads
+//     of the Pi tile (K-major, 64-byte swizzle, 256-row boxes) into a 4-slot ring, all guarded by mbarriers (the
+//     deeper data ring keeps more HBM reads in flight). kind::tf32 takes K-major operands only, so warps 4-7 (one
 //     32-column box each) read every staged element once, fold x^2 into compensated (TwoSum + FMA residual)
 //     column sums, round x to TF32 (cvt.rna) and write it back K-major (64-byte swizzle, conflict-free 16-byte
 //     stores). Warp 1 (one thread) issues tcgen05.mma kind::tf32 with M = 128 data columns and N = 256 sketch
@@ -38,47 +38,41 @@ using namespace tc;
 
 constexpr int TILE_M = 128;        // data columns per CTA (MMA M)
 constexpr int KS = 16;             // data rows per pipeline stage (two K = 8 MMA slices)
-#ifndef SMP_TC_PSTAGES
-#define SMP_TC_PSTAGES 4
-#endif
-#ifndef SMP_TC_ASTAGES
-#define SMP_TC_ASTAGES 4
-#endif
-#ifndef SMP_TC_DSTAGES
-#define SMP_TC_DSTAGES 8
-#endif
-// Three rings: staged data tiles (TMA target, freed by the copy warps), K-major TF32 copies (written by the copy
-// warps, freed by the MMA) and Pi tiles (TMA target, freed by the MMA). The Pi ring is the deepest: a Pi stage
-// comes from L2 in ~1.3 us.
-constexpr int PSTAGES = SMP_TC_PSTAGES;
-constexpr int ASTAGES = SMP_TC_ASTAGES;
-constexpr int DSTAGES = SMP_TC_DSTAGES;
+// Three rings: staged data tiles (TMA target, freed by the copy warps), K-major operand copies (written by the copy
+// warps, freed by the MMA) and Pi tiles (TMA target, freed by the MMA); their depths per operand variant are in Geo.
 constexpr int PI_BOX_ROWS = 256;   // sketch rows per Pi box (MMA N)
 constexpr int MAX_KC = 512;        // sketch rows per CTA (TMEM columns)
-constexpr int DATA_BOX_ROWS = 8;
-constexpr int DATA_BOX_BYTES = 32 * DATA_BOX_ROWS * 4;      // 32 columns x 8 rows, fp32 (one swizzle atom)
+// A stage of data arrives as ONE TMA box of 128 columns x KS rows without swizzle (row t of the stage: 512 contiguous
+// bytes). On this part a 65,536 x 4,000 binary32 block streams at 3.4 TB/s that way over 128 CTAs, against 1.9 TB/s
+// as four 32-column x 8-row 128B-swizzled boxes per 8 rows (a TMA-only probe: the box count per byte, not the bytes
+// in flight, bounds one CTA's stream).
+constexpr int DATA_ROW_BYTES = 128 * 4;
 constexpr int DATA_STAGE_BYTES = 4 * KS * 32 * 4;           // 128 columns x KS rows: [8-row group][32-col box]
-constexpr int KGROUP_BYTES = 4 * DATA_BOX_BYTES;            // one 8-row group of all four boxes
 constexpr int A_STAGE_BYTES = TILE_M * KS * 4;             // K-major copy: 128 rows x 64 B (64-byte swizzle)
 constexpr int PI_BOX_BYTES = PI_BOX_ROWS * KS * 4;          // 256 rows x KS fp32
 // The two operand variants: TF32 (16 data rows per stage, two K = 8 slices per MMA pass) and BF16 operands of
 // binary32 inputs (32 rows per stage, two K = 16 slices). Both give 64-byte K-major operand rows (64-byte swizzle,
-// 8-row groups 512 B apart, 32-byte K slices), the same copy and Pi stage sizes and the same data ring in bytes.
+// 8-row groups 512 B apart, 32-byte K slices) and the same copy and Pi stage sizes. Ring depths (stages of data /
+// copies / Pi) per variant, chosen on the GPU with the variants timed side by side in one process: TF32 4 / 3 / 5
+// (a Pi stage takes ~2 us from L2 while the single-box data stream runs far ahead: 8 / 4 / 4 measured 0.64-0.73 ms
+// per 65,536-row block, 4 / 3 / 5 0.50-0.51 ms); BF16 operands 4 / 4 / 4 (its 16 KB data stages need the depth:
+// 0.35 ms against 0.39 ms with 2 data stages).
 template <bool B16>
 struct Geo {
     static constexpr int KS = B16 ? 32 : 16;
-    static constexpr int DSTAGES = B16 ? SMP_TC_DSTAGES / 2 : SMP_TC_DSTAGES;
+    static constexpr int DSTAGES = 4;
+    static constexpr int ASTAGES = B16 ? 4 : 3;
+    static constexpr int PSTAGES = B16 ? 4 : 5;
     static constexpr int DATA_STAGE_BYTES = 4 * KS * 32 * 4;
+    static constexpr int DRING_BYTES = DSTAGES * DATA_STAGE_BYTES;
+    static constexpr int ARING_BYTES = ASTAGES * TILE_M * 64;
+    static constexpr int PRING_BYTES = PSTAGES * (MAX_KC / PI_BOX_ROWS) * PI_BOX_ROWS * 64;
+    static constexpr int BAR_BYTES = 8 * (2 * (DSTAGES + ASTAGES + PSTAGES) + 1) + 8;   // mbarriers, TMEM address, abort
+    static constexpr int SMEM_BYTES = DRING_BYTES + ARING_BYTES + PRING_BYTES + 1024 /* alignment */ + BAR_BYTES;
+    static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 };
-static_assert(Geo<true>::DSTAGES * Geo<true>::DATA_STAGE_BYTES == DSTAGES * DATA_STAGE_BYTES, "same data ring");
 static_assert(TILE_M * 32 * 2 == A_STAGE_BYTES && PI_BOX_ROWS * 32 * 2 == PI_BOX_BYTES, "same operand stages");
 constexpr int PI_STAGE_BYTES = (MAX_KC / PI_BOX_ROWS) * PI_BOX_BYTES;
-constexpr int DRING_BYTES = DSTAGES * DATA_STAGE_BYTES;
-constexpr int ARING_BYTES = ASTAGES * A_STAGE_BYTES;
-constexpr int PRING_BYTES = PSTAGES * PI_STAGE_BYTES;
-constexpr int BAR_BYTES = 8 * (2 * (DSTAGES + ASTAGES + PSTAGES) + 1) + 8;   // mbarriers, TMEM address, abort flag
-constexpr int SMEM_BYTES = DRING_BYTES + ARING_BYTES + PRING_BYTES + 1024 /* alignment */ + BAR_BYTES;
-static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 constexpr int PI_GEN_SMEM = 8192;  // see generate_pi
 constexpr int PI_ROW_PAD = 64;     // Pi buffers: rows padded to a multiple of 64 (every engine's stage height)
 constexpr int THREADS = 512;       // 16 warps: producers 0 and 2, MMA 1, copy warps on schedulers 0, 2, 3
@@ -151,7 +145,8 @@ struct TcArgs {
     int k, kc, nh;          // sketch rows, TMEM columns used (multiple of 32), Pi boxes per stage
     int n_last;             // N of the last Pi box's MMA (multiple of 16)
     uint32_t tmem_cols;     // power of two >= kc
-    int64_t nrows, rows_per_split;
+    int64_t nrows;
+    int64_t steps;          // KS-row stages of the block (split s takes stages s, s + splits, ...)
     int64_t ldk;
     float* part;            // [splits][ntot][ldk]
     double* nsq;            // [splits][ntot]
@@ -167,14 +162,22 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
                                                                const TcArgs args) {
     constexpr int KS = Geo<B16>::KS;
     constexpr int DSTAGES = Geo<B16>::DSTAGES;
+    constexpr int ASTAGES = Geo<B16>::ASTAGES;
+    constexpr int PSTAGES = Geo<B16>::PSTAGES;
     constexpr int DATA_STAGE_BYTES = Geo<B16>::DATA_STAGE_BYTES;
+    constexpr int DRING_BYTES = Geo<B16>::DRING_BYTES;
+    constexpr int ARING_BYTES = Geo<B16>::ARING_BYTES;
+    constexpr int PRING_BYTES = Geo<B16>::PRING_BYTES;
     extern __shared__ uint8_t smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int split = blockIdx.y;
-    const int64_t rs = (int64_t)split * args.rows_per_split;
-    const int64_t re = min(args.nrows, rs + args.rows_per_split);
-    if (rs >= re) return;
-    const int n_it = (int)((re - rs + KS - 1) / KS);
+    // row splits interleaved by stage: stage it of split s covers rows (it * splits + s) * KS .. + KS, so at any time
+    // all CTAs stream rows from one narrow window of the block (the TMA-only probe: 2.4 against 1.9 TB/s with the
+    // splits' rows contiguous)
+    const int splits = (int)gridDim.y;
+    const int n_it = split < args.steps ? (int)((args.steps - split + splits - 1) / splits) : 0;
+    if (n_it <= 0) return;
+    auto stage_row = [&](int it) { return (int)(((int64_t)it * splits + split) * KS); };
 
     const int tile = blockIdx.x;
     const bool on_b = tile >= args.tiles_a;
@@ -251,14 +254,7 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
             }
             if (lane == 0) {
                 mbar_arrive_expect_tx(dfull_bar(d), DATA_STAGE_BYTES);
-                const int t = (int)(rs + (int64_t)it * KS);
-                const uint32_t dst = dring + d * DATA_STAGE_BYTES;
-#pragma unroll
-                for (int g = 0; g < KS / 8; ++g)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b)
-                        tma_load_2d(dst + g * KGROUP_BYTES + b * DATA_BOX_BYTES, tm_data, (int)col0 + 32 * b,
-                                    t + 8 * g, dfull_bar(d));
+                tma_load_2d(dring + d * DATA_STAGE_BYTES, tm_data, (int)col0, stage_row(it), dfull_bar(d));
             }
             issued = it + 1;
             __syncwarp();
@@ -296,7 +292,7 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
             }
             if (lane == 0) {
                 mbar_arrive_expect_tx(pfull_bar(s), bytes);
-                const int t = (int)(rs + (int64_t)it * KS);
+                const int t = stage_row(it);
                 for (int h = 0; h < args.nh; ++h)
                     tma_load_2d(pring + s * PI_STAGE_BYTES + h * PI_BOX_BYTES, &tm_pi, t, h * PI_BOX_ROWS,
                                 pfull_bar(s));
@@ -371,14 +367,14 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
                 }
                 break;
             }
-            // staged box: 128B swizzle, the 16-byte chunk q of row t sits at chunk q ^ (t & 7)
+            // staged stage: row t at t * 512 B, the warp's 32 columns (128 contiguous bytes: conflict-free) per row
             float x[NG][8];
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
-                const float* box_p = (const float*)(base_ptr + d * DATA_STAGE_BYTES + (grp0 + 2 * g) * KGROUP_BYTES +
-                                                    box * DATA_BOX_BYTES);
+                const float* grp_p = (const float*)(base_ptr + d * DATA_STAGE_BYTES +
+                                                    (grp0 + 2 * g) * 8 * DATA_ROW_BYTES) + box * 32 + lane;
 #pragma unroll
-                for (int t = 0; t < 8; ++t) x[g][t] = box_p[t * 32 + (((lane >> 2) ^ t) << 2) + (lane & 3)];
+                for (int t = 0; t < 8; ++t) x[g][t] = grp_p[t * 128];
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(dempty_bar(d));   // staging read: the producer may refill it
@@ -650,7 +646,8 @@ cudaError_t launch_sketch_tc_pi(smp_ctx* c, const void* A, int64_t lda, const vo
     static std::atomic<bool> attr[2] = {{false}, {false}};
     if (!attr[b16]) {
         cudaError_t e = cudaFuncSetAttribute(b16 ? sketch_tc_kernel<true> : sketch_tc_kernel<false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             b16 ? Geo<true>::SMEM_BYTES : Geo<false>::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr[b16] = true;
     }
@@ -681,12 +678,11 @@ cudaError_t launch_sketch_tc_pi(smp_ctx* c, const void* A, int64_t lda, const vo
     CUtensorMap ma, mb, mp;
     const void* Bp = c->p.same_ab ? A : B;
     const int64_t n2 = c->p.same_ab ? 0 : c->p.n2;
-    // data boxes: 32 columns (128 B, one swizzle row) x 8 rows = DATA_BOX_BYTES, matching the kernel's expect_tx;
+    // data boxes: 128 columns x ks rows, no swizzle = the kernel's DATA_STAGE_BYTES per stage (its expect_tx);
     // Pi boxes: 64-byte rows (16 TF32 or 32 BF16 values) x 256 sketch rows
-    if (!make_map(&ma, A, (uint64_t)c->p.n1, (uint64_t)nrows, (uint64_t)lda, 32, DATA_BOX_ROWS, CU_TENSOR_MAP_SWIZZLE_128B) ||
+    if (!make_map(&ma, A, (uint64_t)c->p.n1, (uint64_t)nrows, (uint64_t)lda, TILE_M, ks, CU_TENSOR_MAP_SWIZZLE_NONE) ||
         !make_map(&mb, Bp, (uint64_t)(c->p.same_ab ? c->p.n1 : c->p.n2), (uint64_t)nrows,
-                  (uint64_t)(c->p.same_ab ? lda : ldb), 32, DATA_BOX_ROWS,
-                  CU_TENSOR_MAP_SWIZZLE_128B) ||
+                  (uint64_t)(c->p.same_ab ? lda : ldb), TILE_M, ks, CU_TENSOR_MAP_SWIZZLE_NONE) ||
         !(b16 ? make_map(&mp, pi, (uint64_t)pi_inner, (uint64_t)pi_rows, (uint64_t)pld, ks, PI_BOX_ROWS,
                          CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2)
               : make_map(&mp, pi, (uint64_t)pi_inner, (uint64_t)pi_rows, (uint64_t)pld, ks, PI_BOX_ROWS,
@@ -709,7 +705,7 @@ cudaError_t launch_sketch_tc_pi(smp_ctx* c, const void* A, int64_t lda, const vo
     const int64_t steps = tpad / ks;
     int splits = std::max(1, std::min(c->splits, c->sm_count / std::max(1, tiles)));
     splits = (int)std::min<int64_t>(splits, steps);
-    a.rows_per_split = ((steps + splits - 1) / splits) * ks;
+    a.steps = steps;
     a.ldk = c->ldk;
     a.part = (float*)c->part;
     a.nsq = c->nsq;
@@ -718,8 +714,8 @@ cudaError_t launch_sketch_tc_pi(smp_ctx* c, const void* A, int64_t lda, const vo
     a.wait_ns = wait > 0 ? (unsigned long long)wait : WAIT_NS;
     a.skip_stage = g_tc_skip_stage.exchange(-1, std::memory_order_relaxed);
     const dim3 grid = smp::counted(dim3((unsigned)tiles, (unsigned)splits));
-    if (b16) sketch_tc_kernel<true><<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, mp, a);
-    else sketch_tc_kernel<false><<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, mp, a);
+    if (b16) sketch_tc_kernel<true><<<grid, THREADS, Geo<true>::SMEM_BYTES, st>>>(ma, mb, mp, a);
+    else sketch_tc_kernel<false><<<grid, THREADS, Geo<false>::SMEM_BYTES, st>>>(ma, mb, mp, a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || buf < 0) return e;
     if (Pi) {   // a caller's Pi: the buffer only becomes free again, nothing is generated ahead

@@ -8,9 +8,8 @@ run exactly that configuration and compare with the oracle (never with another G
    Precision shape (n1 = n2 = 4,096, k = 1,024: the sketch rows split over two CTAs): BF16 within 1e-2; FP8 within
    2e-3 of the quantised model (the oracle's Pi and the block rounded to E4M3 on the host) and within 8e-2 of the
    exact oracle. Column norms: compensated binary32 sums of the unrounded inputs (TwoSum plus the FMA residual, the
-   low parts summed in binary32) over R rows carry a relative error of at most about R u^2 (u = 2^-24), i.e.
-   6e-11 for a 65,536-row block summed in 4 row splits of 16,384 rows: 1e-12 where the engine splits each column's
-   rows over several accumulators (the scale shape), 1e-10 for the BF16 / FP8 engines at the precision shape.
+   low parts summed in binary32) over R rows carry a relative error of at most about R u^2 (u = 2^-24); with
+   R <= 16,384 rows per accumulator (a 65,536-row block in 4 row splits) that is 6e-11: 1e-10 for every engine.
 2. The scale workload end to end at full size (d = 1,000,000 in 16 blocks, the last one ragged), and its A = B
    (PCA) case: Omega bit-exact against the oracle run on the same bytes (so the compensated norms summed over 16
    blocks and the row splits flip no coin), every sketch column within 2e-3, relative spectral error within 1e-3
@@ -113,8 +112,8 @@ def test_scale_block_matches_oracle(env, scale_block, engine, tol):
     st = s.sketch_state()
     assert _colrel(st["At"].cpu().numpy().astype(np.float64), ref.At.T) < tol
     assert _colrel(st["Bt"].cpu().numpy().astype(np.float64), ref.Bt.T) < tol
-    np.testing.assert_allclose(st["sA"].cpu().numpy(), ref.sA, rtol=1e-12)
-    np.testing.assert_allclose(st["sB"].cpu().numpy(), ref.sB, rtol=1e-12)
+    np.testing.assert_allclose(st["sA"].cpu().numpy(), ref.sA, rtol=1e-10)
+    np.testing.assert_allclose(st["sB"].cpu().numpy(), ref.sB, rtol=1e-10)
     s.close()
 
 
@@ -224,8 +223,8 @@ def test_scale_workload_end_to_end(env, pool, scale_data, same_ab):
                               w["n"], w["n"], w["k"], 1, BLOCK, same_ab=same_ab, pool=pool)
     ref = OS.solve_from_state(ref_st, m, w["r"], w["T"], 2)
 
-    np.testing.assert_allclose(gsA, ref_st.sA, rtol=1e-12)
-    np.testing.assert_allclose(gsB, ref_st.sB, rtol=1e-12)
+    np.testing.assert_allclose(gsA, ref_st.sA, rtol=1e-10)
+    np.testing.assert_allclose(gsB, ref_st.sB, rtol=1e-10)
     assert _colrel(gA, ref_st.At.T) < 2e-3
     assert _colrel(gB, ref_st.Bt.T) < 2e-3
     assert om["nnz"] == ref["rows"].shape[0]
