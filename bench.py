@@ -857,7 +857,7 @@ def run_precision(args, w, embed=False):
             results[name]["spectral_err"] = e
     prefix = None
     if not args.no_cpu_baseline:
-        d0 = 200_000
+        d0 = min(200_000, w["d"])
         Ap, Bp = A[:d0], B[:d0]
         res, fac = {}, []
         for name, eng in (("bf16", smp.SMP_ENGINE_TC), ("fp8_e4m3", smp.SMP_ENGINE_TC_FP8)):

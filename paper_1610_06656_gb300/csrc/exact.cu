@@ -288,7 +288,8 @@ __global__ void __launch_bounds__(256) transpose_tf32_kernel(const float* __rest
 
 struct ExactArgs {
     int64_t n1, n2;                 // columns i of A, columns j of B
-    int64_t nrows, rows_per_split;
+    int64_t nrows;
+    int64_t steps;          // KS-row stages of the block (split s takes stages s, s + splits, ...)
     const int64_t* col_ptr;         // CSC of Omega
     const int32_t* csc_row;
     double* part;                   // [splits][ld], CSC order
@@ -302,10 +303,11 @@ __global__ void __launch_bounds__(THREADS, 1) exact_tc_kernel(const __grid_const
     extern __shared__ uint8_t smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int split = blockIdx.y;
-    const int64_t rs = (int64_t)split * args.rows_per_split;
-    const int64_t re = min(args.nrows, rs + args.rows_per_split);
-    if (rs >= re) return;
-    const int n_it = (int)((re - rs + KS - 1) / KS);
+    // row splits interleaved by pipeline stage (stage it of split s: rows (it * splits + s) * KS ..), so all CTAs
+    // stream rows from one narrow window of the block (better DRAM locality than contiguous splits)
+    const int splits = (int)gridDim.y;
+    const int n_it = split < args.steps ? (int)((args.steps - split + splits - 1) / splits) : 0;
+    if (n_it <= 0) return;
     const int64_t j0 = (int64_t)blockIdx.x * TILE_M;
     const int64_t i0 = (int64_t)blockIdx.z * MAX_NI;
     const int ni = (int)min((int64_t)MAX_NI, args.n1 - i0);      // columns i of this CTA
@@ -372,7 +374,7 @@ __global__ void __launch_bounds__(THREADS, 1) exact_tc_kernel(const __grid_const
             }
             if (lane == 0) {
                 mbar_arrive_expect_tx(dfull_bar(d), DATA_STAGE_BYTES);
-                const int t = (int)(rs + (int64_t)it * KS);
+                const int t = (int)(((int64_t)it * splits + split) * KS);
                 const uint32_t dst = dring + d * DATA_STAGE_BYTES;
 #pragma unroll
                 for (int g = 0; g < KS / 8; ++g)
@@ -401,7 +403,7 @@ __global__ void __launch_bounds__(THREADS, 1) exact_tc_kernel(const __grid_const
             }
             if (lane == 0) {
                 mbar_arrive_expect_tx(pfull_bar(s), bytes);
-                const int t = (int)(rs + (int64_t)it * KS);
+                const int t = (int)(((int64_t)it * splits + split) * KS);
                 for (int h = 0; h < nh; ++h)
                     tma_load_2d(pring + s * AT_STAGE_BYTES + h * AT_BOX_BYTES, &tm_at, t,
                                 (int)i0 + h * AT_BOX_ROWS, pfull_bar(s));
@@ -628,8 +630,7 @@ cudaError_t launch_exact(smp_ctx* c, const void* A, int64_t lda, const void* B, 
     const int64_t steps = (nrows + KS - 1) / KS;
     int splits = std::max(1, std::min(EXACT_SPLITS, c->sm_count / std::max(1, tiles * chunks)));
     splits = (int)std::min<int64_t>(splits, steps);
-    a.rows_per_split = ((steps + splits - 1) / splits) * KS;
-    splits = (int)((nrows + a.rows_per_split - 1) / a.rows_per_split);
+    a.steps = steps;
     exact_tc_kernel<<<smp::counted(dim3((unsigned)tiles, (unsigned)splits, (unsigned)chunks)), THREADS, SMEM_BYTES,
                       c->stream>>>(mb, mat, a);
     return cudaGetLastError();

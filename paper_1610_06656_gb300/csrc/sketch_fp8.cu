@@ -150,7 +150,8 @@ struct Fp8Args {
     int tiles_a;
     int k, kmma;
     uint32_t tmem_cols;
-    int64_t nrows, rows_per_split;
+    int64_t nrows;
+    int64_t steps;          // KS-row stages of the block (split s takes stages s, s + splits, ...)
     int64_t ldk;
     float* part;
     double* nsq;
@@ -167,11 +168,12 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_fp8_kernel(const __grid_con
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int split = blockIdx.y;
     const int kh = blockIdx.z;
-    const int64_t rs = (int64_t)split * args.rows_per_split;
-    const int64_t re = min(args.nrows, rs + args.rows_per_split);
+    // row splits interleaved by pipeline stage (stage it of split s: rows (it * splits + s) * KS ..), so all CTAs
+    // stream rows from one narrow window of the block (better DRAM locality than contiguous splits)
+    const int splits = (int)gridDim.y;
+    const int n_it = split < args.steps ? (int)((args.steps - split + splits - 1) / splits) : 0;
     const int n_cta = min(KC_CTA, args.kmma - kh * KC_CTA);
-    if (rs >= re || n_cta <= 0) return;
-    const int n_it = (int)((re - rs + KS - 1) / KS);
+    if (n_it <= 0 || n_cta <= 0) return;
     const int nh = (n_cta + MMA_N - 1) / MMA_N;
     const int n_last = n_cta - (nh - 1) * MMA_N;
     const int kc_cta = min(KC_CTA, (args.k + 31) / 32 * 32 - kh * KC_CTA);
@@ -245,7 +247,7 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_fp8_kernel(const __grid_con
             }
             if (lane == 0) {
                 mbar_arrive_expect_tx(dfull_bar(d), DATA_STAGE_BYTES);
-                const int t = (int)(rs + (int64_t)it * KS);
+                const int t = (int)(((int64_t)it * splits + split) * KS);
                 const uint32_t dst = dring + d * DATA_STAGE_BYTES;
 #pragma unroll
                 for (int g = 0; g < KS / 8; ++g)
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_fp8_kernel(const __grid_con
             }
             if (lane == 0) {
                 mbar_arrive_expect_tx(pfull_bar(s), bytes);
-                const int t = (int)(rs + (int64_t)it * KS);
+                const int t = (int)(((int64_t)it * splits + split) * KS);
                 for (int h = 0; h < nh; ++h)
                     tma_load_2d(pring + s * PI_STAGE_BYTES + h * PI_BOX_BYTES, &tm_pi, t, kh * KC_CTA + h * MMA_N,
                                 pfull_bar(s));
@@ -499,7 +501,7 @@ cudaError_t launch_sketch_fp8(smp_ctx* c, const void* A, int64_t lda, const void
     const int64_t steps = tpad / KS;
     int splits = std::max(1, std::min(c->splits, c->sm_count / std::max(1, tiles * khalves)));
     splits = (int)std::min<int64_t>(splits, steps);
-    a.rows_per_split = ((steps + splits - 1) / splits) * KS;
+    a.steps = steps;
     a.ldk = c->ldk;
     a.part = (float*)c->part;
     a.nsq = c->nsq;
