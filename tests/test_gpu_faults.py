@@ -80,21 +80,22 @@ def test_injected_allocation_failures(env):
         smp.smp_debug_fail_allocs(0)
 
 
-@pytest.mark.parametrize("engine", ["tc", "tc_bf16"])
-def test_bounded_wait_runs_out(env, engine):
+@pytest.mark.parametrize("engine,n1,n2", [("tc", 200, 136), ("tc_bf16", 200, 136), ("tc", 512, 512),
+                                          ("tc_bf16", 640, 520)])
+def test_bounded_wait_runs_out(env, engine, n1, n2):
     """The tensor-core kernel with a 1 ms wait limit and the data loads of stage 3 never issued: its waits on that
     stage give up, the error word reports the timeout (SMP_ETIMEOUT from smp_sync), and a normal sketch on the same
-    context afterwards matches the oracle."""
+    context afterwards matches the oracle; on 4 to 10 column tiles."""
     torch, smp, pipeline = env
     eng = {"tc": smp.SMP_ENGINE_TC, "tc_bf16": smp.SMP_ENGINE_TC_BF16}[engine]
     tol = 2e-3 if engine == "tc" else 1e-2
-    A, B = synth.lowrank_plus_noise(1024, 200, 136, 5, 0.1, 0.5, seed=6, dtype=np.float32)
+    A, B = synth.lowrank_plus_noise(1024, n1, n2, 5, 0.1, 0.5, seed=6, dtype=np.float32)
     Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
-    s = pipeline.Solver(200, 136, 64, torch.float32, seed=1, engine=eng, max_rows=1024)
+    s = pipeline.Solver(n1, n2, 64, torch.float32, seed=1, engine=eng, max_rows=1024)
     try:
         smp.smp_debug_tc_wait(1_000_000, 3)
         smp.smp_sketch_reset(s.ctx)
-        smp.smp_sketch_accumulate(s.ctx, Ad, 200, Bd, 136, 0, 1024)
+        smp.smp_sketch_accumulate(s.ctx, Ad, n1, Bd, n2, 0, 1024)
         with pytest.raises(smp.SmpError) as e:
             smp.smp_sync(s.ctx)
         assert e.value.status == smp.SMP_ETIMEOUT

@@ -29,8 +29,9 @@ def _colrel(X, Y):
     return float((num / den).max())
 
 
+# the last two cases cover 10 and 8 column tiles over both matrices (a ragged tile on each)
 @pytest.mark.parametrize("k,n1,n2,nrows", [(300, 200, 132, 100), (512, 256, 128, 64), (40, 36, 68, 16),
-                                           (500, 132, 200, 333)])
+                                           (500, 132, 200, 333), (300, 640, 520, 200), (64, 512, 512, 48)])
 def test_tc_exact_on_integers(env, k, n1, n2, nrows):
     torch, smp, pipeline = env
     rng = np.random.default_rng(k + n1)
