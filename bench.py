@@ -52,7 +52,7 @@ WORKLOADS = {
     # batched form: 256 FP32 instances (n in [64, 2048], d in [1e4, 5e5], r in {5, 10, 20}, k = 8 r) solved
     # together, sketch engine per (k, n bucket) from the autotuner
     "batch": dict(instances=256, warm=16, block=65536, pool_rows=1_000_000, width=2048, L=20, sigma=0.1, alpha=0.5,
-                  budget=200e9, workers=16, T=10),
+                  budget=200e9, workers=32, T=10),
 }
 
 
@@ -904,7 +904,7 @@ def run_batched(args, w, embed=False):
     # many jobs run on streams of their own: let more of them reach the device concurrently (process-local)
     os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     import torch
-    from paper_1610_06656_gb300 import batch, build, smp, synth
+    from paper_1610_06656_gb300 import batch, build, serve, smp, synth
     smp.load(build.build())
     torch.cuda.set_device(0)
     bf16 = args.batch_dtype == "bf16"
@@ -955,7 +955,8 @@ def run_batched(args, w, embed=False):
                        "d": "uniform [10000, 500000]", "r": [5, 10, 20], "k": "8 r", "T": w["T"],
                        "block_rows": w["block"], "solve_workers": workers, "engines": engines,
                        "autotune_s": t_tune, "autotune_trials": tuner.trials},
-            "wall_s": wall, "input_gb": streamed / 1e9, "input_gbs": streamed / wall / 1e9,
+            "wall_s": wall, "phases": getattr(serve.run_staged, "last_phases", None),
+            "input_gb": streamed / 1e9, "input_gbs": streamed / wall / 1e9,
             "hbm_frac": streamed / wall / 1e9 / peaks["hbm_gbs"], "hbm_peak_kind": peak_kind,
             "p50_ms": statistics.median(lat), "p99_ms": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
             "gpu_launches": int(launches), "clocks": clk, "roofline": None, "cpu_baseline": None, "e2e": None}

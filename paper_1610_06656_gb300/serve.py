@@ -133,6 +133,7 @@ def run_staged(server, jobs, pool_A, pool_B, dtype, block_rows=32768, engine=S.S
     records = []
     lda = pool_A.stride(0)
     t0 = time.perf_counter()
+    phases = {"sketch_s": 0.0, "solve_s": 0.0, "waves": 0}
     while pending:
         if time.perf_counter() - t0 > time_limit:
             raise RuntimeError("batched run exceeded %.0f s" % time_limit)
@@ -144,6 +145,8 @@ def run_staged(server, jobs, pool_A, pool_B, dtype, block_rows=32768, engine=S.S
             wave.append((jid, pending.popleft()))
         if not wave:
             raise RuntimeError("a single job does not fit the server's memory budget")
+        phases["waves"] += 1
+        tw = time.perf_counter()
         plans = [block_plan(spec.d, block_rows) for _, spec in wave]
         for p in range(max(len(pl) for pl in plans)):
             for (jid, spec), pl in zip(wave, plans):
@@ -154,6 +157,8 @@ def run_staged(server, jobs, pool_A, pool_B, dtype, block_rows=32768, engine=S.S
                     S.smp_serve_block(server, jid, a, lda, b, lda, r0, nr)
         if sync is not None:
             sync()
+        ts = time.perf_counter()
+        phases["sketch_s"] += ts - tw
         for jid, _ in wave:
             S.smp_serve_close(server, jid)
         for jid, spec in wave:
@@ -162,6 +167,8 @@ def run_staged(server, jobs, pool_A, pool_B, dtype, block_rows=32768, engine=S.S
                 U, Sv, V = keep[spec.idx]
             nnz, lat = S.smp_serve_collect(server, jid, U, Sv, V)
             records.append(dict(idx=spec.idx, latency_ms=lat, nnz=nnz, done_at=time.perf_counter() - t0))
+        phases["solve_s"] += time.perf_counter() - ts
     wall = max(r["done_at"] for r in records) if records else 0.0
+    run_staged.last_phases = phases
     return records, wall
 
