@@ -360,6 +360,7 @@ __global__ void __launch_bounds__(THREADS, 1) exact_tc_kernel(const __grid_const
     if (warp == 0) {
         // ---------------- B producer: 128 columns x KS rows of B per stage into the staging ring
         if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_b) : "memory");
+        int issued = 0;
         for (int it = 0; it < n_it; ++it) {
             const int d = it % DSTAGES;
             const uint32_t ph = (uint32_t)(it / DSTAGES) & 1u;
@@ -383,12 +384,17 @@ __global__ void __launch_bounds__(THREADS, 1) exact_tc_kernel(const __grid_const
                         tma_load_2d(dst + g * KGROUP_BYTES + b * DATA_BOX_BYTES, &tm_b, (int)j0 + 32 * b, t + 8 * g,
                                     dfull_bar(d));
             }
+            issued = it + 1;
             __syncwarp();
         }
+        // the CTA may not finish while a load it issued is still landing (even after an abort)
+        for (int it = max(0, issued - DSTAGES); it < issued; ++it)
+            mbar_wait_landed(dfull_bar(it % DSTAGES), (uint32_t)(it / DSTAGES) & 1u, WAIT_NS);
     } else if (warp == 2) {
         // ---------------- A^T producer: nh boxes of 256 columns i x KS rows per stage
         if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_at) : "memory");
         const uint32_t bytes = nh * AT_BOX_BYTES;
+        int issued = 0;
         for (int it = 0; it < n_it; ++it) {
             const int s = it % PSTAGES;
             const uint32_t ph = (uint32_t)(it / PSTAGES) & 1u;
@@ -408,8 +414,11 @@ __global__ void __launch_bounds__(THREADS, 1) exact_tc_kernel(const __grid_const
                     tma_load_2d(pring + s * AT_STAGE_BYTES + h * AT_BOX_BYTES, &tm_at, t,
                                 (int)i0 + h * AT_BOX_ROWS, pfull_bar(s));
             }
+            issued = it + 1;
             __syncwarp();
         }
+        for (int it = max(0, issued - PSTAGES); it < issued; ++it)
+            mbar_wait_landed(pfull_bar(it % PSTAGES), (uint32_t)(it / PSTAGES) & 1u, WAIT_NS);
     } else if (warp == 1) {
         // ---------------- MMA issuer: D[j][i] += sum_t B[t][j] A[t][i] (lane 0 issues)
         const uint32_t id_full = idesc_tf32(TILE_M, AT_BOX_ROWS);

@@ -150,7 +150,8 @@ cudaError_t launch_sketch_simt_into(int dtype, const void* A, int64_t lda, const
 bool tc_supported(const smp_ctx* c);
 void release_tc(smp_ctx* c);   // waits for the side stream, frees the Pi buffers, stream and events
 cudaError_t tc_speculate_first_block(smp_ctx* c);   // after a reset: Pi of rows [0, last block size) ahead of time
-// Generated Pi of the tensor-core engines: kpad rows (a multiple of 256, zero beyond k) x ld columns (row stride),
+// Generated Pi of the tensor-core engines: kpad rows (round_up(k, 16) up to 256 for binary32 contexts, else a
+// multiple of 256; zero beyond k) x ld columns (row stride),
 // esize bytes per element (4: TF32 in binary32 containers, 2: BF16, 1: E4M3).
 struct PiGeom {
     int kpad;

@@ -153,6 +153,7 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_bf16_kernel(const __grid_co
     if (warp == 0) {
         // ---------------- data producer (lane 0 issues)
         if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)tm_data) : "memory");
+        int issued = 0;
         for (int it = 0; it < n_it; ++it) {
             const int d = it % DSTAGES;
             const uint32_t ph = (uint32_t)(it / DSTAGES) & 1u;
@@ -176,12 +177,17 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_bf16_kernel(const __grid_co
                         tma_load_2d(dst + grp_off(g * (BOX_ROWS / 8), b), tm_data, (int)col0 + BOX_COLS * b,
                                     t + BOX_ROWS * g, dfull_bar(d));
             }
+            issued = it + 1;
             __syncwarp();
         }
+        // the CTA may not finish while a load it issued is still landing (even after an abort)
+        for (int it = max(0, issued - DSTAGES); it < issued; ++it)
+            mbar_wait_landed(dfull_bar(it % DSTAGES), (uint32_t)(it / DSTAGES) & 1u, WAIT_NS);
     } else if (warp == 2) {
         // ---------------- Pi producer: this CTA's sketch rows kh * 512 ...
         if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_pi) : "memory");
         const uint32_t bytes = nh * PI_BOX_BYTES;
+        int issued = 0;
         for (int it = 0; it < n_it; ++it) {
             const int s = it % PSTAGES;
             const uint32_t ph = (uint32_t)(it / PSTAGES) & 1u;
@@ -201,8 +207,11 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_bf16_kernel(const __grid_co
                     tma_load_2d(pring + s * PI_STAGE_BYTES + h * PI_BOX_BYTES, &tm_pi, t,
                                 kh * KC_CTA + h * MMA_N, pfull_bar(s));
             }
+            issued = it + 1;
             __syncwarp();
         }
+        for (int it = max(0, issued - PSTAGES); it < issued; ++it)
+            mbar_wait_landed(pfull_bar(it % PSTAGES), (uint32_t)(it / PSTAGES) & 1u, WAIT_NS);
     } else if (warp == 1) {
         // ---------------- MMA issuer (the whole warp waits; lane 0 issues)
         const uint32_t id_full = idesc_bf16(TILE_M, MMA_N, true);

@@ -233,6 +233,7 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_fp8_kernel(const __grid_con
     if (warp == 0) {
         // ---------------- data producer: BF16 tiles into the staging ring (lane 0 issues)
         if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)tm_data) : "memory");
+        int issued = 0;
         for (int it = 0; it < n_it; ++it) {
             const int d = it % DSTAGES;
             const uint32_t ph = (uint32_t)(it / DSTAGES) & 1u;
@@ -256,12 +257,17 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_fp8_kernel(const __grid_con
                         tma_load_2d(dst + g * KGROUP_BYTES + b * BOX_BYTES, tm_data, (int)col0 + BOX_COLS * b,
                                     t + 8 * g, dfull_bar(d));
             }
+            issued = it + 1;
             __syncwarp();
         }
+        // the CTA may not finish while a load it issued is still landing (even after an abort)
+        for (int it = max(0, issued - DSTAGES); it < issued; ++it)
+            mbar_wait_landed(dfull_bar(it % DSTAGES), (uint32_t)(it / DSTAGES) & 1u, WAIT_NS);
     } else if (warp == 2) {
         // ---------------- Pi producer: E4M3 tiles of this CTA's sketch rows
         if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_pi) : "memory");
         const uint32_t bytes = nh * PI_BOX_BYTES;
+        int issued = 0;
         for (int it = 0; it < n_it; ++it) {
             const int s = it % PSTAGES;
             const uint32_t ph = (uint32_t)(it / PSTAGES) & 1u;
@@ -281,8 +287,11 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_fp8_kernel(const __grid_con
                     tma_load_2d(pring + s * PI_STAGE_BYTES + h * PI_BOX_BYTES, &tm_pi, t, kh * KC_CTA + h * MMA_N,
                                 pfull_bar(s));
             }
+            issued = it + 1;
             __syncwarp();
         }
+        for (int it = max(0, issued - PSTAGES); it < issued; ++it)
+            mbar_wait_landed(pfull_bar(it % PSTAGES), (uint32_t)(it / PSTAGES) & 1u, WAIT_NS);
     } else if (warp == 1) {
         // ---------------- MMA issuer (the whole warp waits; lane 0 issues)
         const uint32_t id_full = idesc_e4m3(TILE_M, MMA_N, true);

@@ -8,13 +8,12 @@
 //     (sketch row, data row); regenerating it inside each column tile would cost (n1 + n2) / 128 times more.
 //  2. sketch_tc_kernel: one CTA per (128-column tile, row split; the splits interleaved by pipeline stage). Warp 0
 //     issues one TMA load per stage of the data tile (rows of A are contiguous along the columns, so the tile lands
-//     column-major: one 128-column x KS-row box, no swizzle) into an 8-slot staging ring; warp 2 issues TMA loads
-//     of the Pi tile (K-major, 64-byte swizzle, 256-row boxes) into a 4-slot ring, all guarded by mbarriers (the
-//     deeper data ring keeps more HBM reads in flight). kind::tf32 takes K-major operands only, so warps 4-7 (one
-//     32-column box each) read every staged element once, fold x^2 into compensated (TwoSum + FMA residual)
-//     column sums, round x to TF32 (cvt.rna) and write it back K-major (64-byte swizzle, conflict-free 16-byte
-//     stores). Warp 1 (one thread) issues tcgen05.mma kind::tf32 with M = 128 data columns and N = 256 sketch
-//     rows per instruction into a TMEM accumulator of 128 lanes x up to 512 columns. Warps 4-7 then drain TMEM
+//     column-major: one 128-column x KS-row box, no swizzle) into a staging ring; warp 2 issues the TMA loads of
+//     the stage's Pi tile (K-major, swizzled, up to 256-row boxes) into a Pi ring, all guarded by mbarriers. kind::tf32 takes K-major operands only, so eight copy warps (a 32-column
+//     box and two 8-row groups each) read every staged element once, fold x^2 into compensated (TwoSum + FMA
+//     residual) column sums, round x to TF32 (cvt.rna) and write it back K-major (swizzled, conflict-free 16-byte
+//     stores). Warp 1 (one thread) issues tcgen05.mma kind::tf32 with M = 128 data columns and N = up to 256 sketch
+//     rows per instruction into a TMEM accumulator of 128 lanes x up to 512 columns. All 16 warps then drain TMEM
 //     with tcgen05.ld and add the tile into the split's partial sketch. Every wait is bounded (%globaltimer, the
 //     limit a kernel argument): a timeout sets the device error word and raises the CTA's abort flag; every role
 //     leaves its loop, the producers wait (bounded) until the loads they issued have landed, the MMA warp commits
@@ -37,42 +36,48 @@ namespace {
 using namespace tc;
 
 constexpr int TILE_M = 128;        // data columns per CTA (MMA M)
-constexpr int KS = 16;             // data rows per pipeline stage (two K = 8 MMA slices)
 // Three rings: staged data tiles (TMA target, freed by the copy warps), K-major operand copies (written by the copy
 // warps, freed by the MMA) and Pi tiles (TMA target, freed by the MMA); their depths per operand variant are in Geo.
 constexpr int PI_BOX_ROWS = 256;   // sketch rows per Pi box (MMA N)
 constexpr int MAX_KC = 512;        // sketch rows per CTA (TMEM columns)
-// A stage of data arrives as ONE TMA box of 128 columns x KS rows without swizzle (row t of the stage: 512 contiguous
-// bytes). On this part a 65,536 x 4,000 binary32 block streams at 3.4 TB/s that way over 128 CTAs, against 1.9 TB/s
-// as four 32-column x 8-row 128B-swizzled boxes per 8 rows (a TMA-only probe: the box count per byte, not the bytes
-// in flight, bounds one CTA's stream).
+// One TMA load moves a whole stage of data: a 128-column x KS-row box without swizzle (row t of the stage: 512
+// contiguous bytes), landing column-major. A CTA completes about four TMA loads per microsecond however many are in
+// flight (a TMA-only stream on this part: 33 GB/s per CTA with 8 KB boxes at 4 to 24 in flight, 55 GB/s with 16 KB
+// boxes, where 128 CTAs reach 7 TB/s), so the box count per byte bounds one CTA's stream.
 constexpr int DATA_ROW_BYTES = 128 * 4;
-constexpr int DATA_STAGE_BYTES = 4 * KS * 32 * 4;           // 128 columns x KS rows: [8-row group][32-col box]
-constexpr int A_STAGE_BYTES = TILE_M * KS * 4;             // K-major copy: 128 rows x 64 B (64-byte swizzle)
-constexpr int PI_BOX_BYTES = PI_BOX_ROWS * KS * 4;          // 256 rows x KS fp32
-// The two operand variants: TF32 (16 data rows per stage, two K = 8 slices per MMA pass) and BF16 operands of
-// binary32 inputs (32 rows per stage, two K = 16 slices). Both give 64-byte K-major operand rows (64-byte swizzle,
-// 8-row groups 512 B apart, 32-byte K slices) and the same copy and Pi stage sizes. Ring depths (stages of data /
-// copies / Pi) per variant, chosen on the GPU with the variants timed side by side in one process: TF32 4 / 3 / 5
-// (a Pi stage takes ~2 us from L2 while the single-box data stream runs far ahead: 8 / 4 / 4 measured 0.64-0.73 ms
-// per 65,536-row block, 4 / 3 / 5 0.50-0.51 ms); BF16 operands 4 / 4 / 4 (its 16 KB data stages need the depth:
-// 0.35 ms against 0.39 ms with 2 data stages).
-template <bool B16>
+// Operand variants. K-major operand rows hold the KS values of a stage (TF32 in 32-bit containers or BF16): 64-byte
+// rows take the 64-byte swizzle (8-row groups 512 B apart), 128-byte rows the 128-byte swizzle (groups 1,024 B apart);
+// an MMA K slice is 32 B of the row (8 TF32 or 16 BF16 values).
+//  - TF32, k > SMALL_KC: 16-row stages (8 KB of data, a 32 KB Pi stage at k = 512 in two 256-row boxes), rings of
+//    data / copies / Pi 4 / 3 / 5: a Pi stage takes ~1-2 us from L2, and 32-row stages (64 KB of Pi each) leave room
+//    for only two in flight (0.52 against 0.50 ms per 65,536 x 4,000 block).
+//  - TF32, k <= SMALL_KC (the batched and serving sizes, k = 8 r <= 160): 32-row stages (one 16 KB data box, a Pi box
+//    of round_up(k, 16) rows, four MMA slices), rings 4 / 3 / 4. Against 16-row stages: 0.31 against 0.42 ms per
+//    65,536-row block at n = 2,048, k = 40; 3.75 against 2.9 TB/s over 24 concurrent mixed blocks.
+//  - BF16 operands of binary32 inputs: 32-row stages of 64-byte rows, rings 4 / 4 / 4 (k > SMALL_KC) or 6 / 4 / 8.
+constexpr int SMALL_KC = 160;
+template <bool B16, bool SMALL = false>
 struct Geo {
-    static constexpr int KS = B16 ? 32 : 16;
-    static constexpr int DSTAGES = 4;
+    static constexpr int KS = (B16 || SMALL) ? 32 : 16;      // data rows per pipeline stage
+    static constexpr int ROWB = KS * (B16 ? 2 : 4);           // bytes of one K-major operand row
+    static constexpr uint32_t SWZ = ROWB == 128 ? SWZ_128B : SWZ_64B;
+    static constexpr uint32_t SBO = 8 * ROWB;                // 8-row group stride of the operand layouts
+    static constexpr int KSLICES = ROWB / 32;                // MMA K slices per stage
+    static constexpr int DSTAGES = B16 ? (SMALL ? 6 : 4) : 4;
     static constexpr int ASTAGES = B16 ? 4 : 3;
-    static constexpr int PSTAGES = B16 ? 4 : 5;
-    static constexpr int DATA_STAGE_BYTES = 4 * KS * 32 * 4;
+    static constexpr int PSTAGES = B16 ? (SMALL ? 8 : 4) : (SMALL ? 4 : 5);
+    static constexpr int DATA_STAGE_BYTES = 4 * KS * 32 * 4; // 128 columns x KS rows: [8-row group][32-col box]
+    static constexpr int A_SLOT_BYTES = TILE_M * ROWB;
+    static constexpr int PI_BOX_BYTES = PI_BOX_ROWS * ROWB;  // a full 256-row box
+    static constexpr int PI_SLOT_BYTES = SMALL ? SMALL_KC * ROWB : (MAX_KC / PI_BOX_ROWS) * PI_BOX_BYTES;
     static constexpr int DRING_BYTES = DSTAGES * DATA_STAGE_BYTES;
-    static constexpr int ARING_BYTES = ASTAGES * TILE_M * 64;
-    static constexpr int PRING_BYTES = PSTAGES * (MAX_KC / PI_BOX_ROWS) * PI_BOX_ROWS * 64;
+    static constexpr int ARING_BYTES = ASTAGES * A_SLOT_BYTES;
+    static constexpr int PRING_BYTES = PSTAGES * PI_SLOT_BYTES;
     static constexpr int BAR_BYTES = 8 * (2 * (DSTAGES + ASTAGES + PSTAGES) + 1) + 8;   // mbarriers, TMEM address, abort
     static constexpr int SMEM_BYTES = DRING_BYTES + ARING_BYTES + PRING_BYTES + 1024 /* alignment */ + BAR_BYTES;
     static_assert(SMEM_BYTES <= 232448, "shared memory budget");
+    static_assert(PI_SLOT_BYTES % 1024 == 0 && A_SLOT_BYTES % 1024 == 0, "slots keep the swizzle atoms aligned");
 };
-static_assert(TILE_M * 32 * 2 == A_STAGE_BYTES && PI_BOX_ROWS * 32 * 2 == PI_BOX_BYTES, "same operand stages");
-constexpr int PI_STAGE_BYTES = (MAX_KC / PI_BOX_ROWS) * PI_BOX_BYTES;
 constexpr int PI_GEN_SMEM = 8192;  // see generate_pi
 constexpr int PI_ROW_PAD = 64;     // Pi buffers: rows padded to a multiple of 64 (every engine's stage height)
 constexpr int THREADS = 512;       // 16 warps: producers 0 and 2, MMA 1, copy warps on schedulers 0, 2, 3
@@ -144,6 +149,7 @@ struct TcArgs {
     int tiles_a;            // column tiles over A; tiles over B follow
     int k, kc, nh;          // sketch rows, TMEM columns used (multiple of 32), Pi boxes per stage
     int n_last;             // N of the last Pi box's MMA (multiple of 16)
+    int pbox;               // sketch rows per Pi box: 256, or round_up(k, 16) when one box covers k
     uint32_t tmem_cols;     // power of two >= kc
     int64_t nrows;
     int64_t steps;          // KS-row stages of the block (split s takes stages s, s + splits, ...)
@@ -155,19 +161,23 @@ struct TcArgs {
     int skip_stage;               // test hook: the data producer issues nothing from this stage on (-1: never)
 };
 
-template <bool B16>
+template <bool B16, bool SMALL>
 __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_constant__ CUtensorMap tm_a,
                                                                const __grid_constant__ CUtensorMap tm_b,
                                                                const __grid_constant__ CUtensorMap tm_pi,
                                                                const TcArgs args) {
-    constexpr int KS = Geo<B16>::KS;
-    constexpr int DSTAGES = Geo<B16>::DSTAGES;
-    constexpr int ASTAGES = Geo<B16>::ASTAGES;
-    constexpr int PSTAGES = Geo<B16>::PSTAGES;
-    constexpr int DATA_STAGE_BYTES = Geo<B16>::DATA_STAGE_BYTES;
-    constexpr int DRING_BYTES = Geo<B16>::DRING_BYTES;
-    constexpr int ARING_BYTES = Geo<B16>::ARING_BYTES;
-    constexpr int PRING_BYTES = Geo<B16>::PRING_BYTES;
+    using G = Geo<B16, SMALL>;
+    constexpr int KS = G::KS;
+    constexpr int DATA_STAGE_BYTES = G::DATA_STAGE_BYTES;
+    constexpr int DSTAGES = G::DSTAGES;
+    constexpr int ASTAGES = G::ASTAGES;
+    constexpr int PSTAGES = G::PSTAGES;
+    constexpr int DRING_BYTES = G::DRING_BYTES;
+    constexpr int ARING_BYTES = G::ARING_BYTES;
+    constexpr int PRING_BYTES = G::PRING_BYTES;
+    constexpr int PI_SLOT_BYTES = G::PI_SLOT_BYTES;
+    constexpr int A_SLOT_BYTES = G::A_SLOT_BYTES;
+    constexpr int PI_BOX_BYTES = G::PI_BOX_BYTES;
     extern __shared__ uint8_t smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int split = blockIdx.y;
@@ -192,8 +202,8 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t* base_ptr = smem_raw + (base - raw);
     const uint32_t dring = base;                        // DSTAGES x DATA_STAGE_BYTES
-    const uint32_t aring = base + DRING_BYTES;          // ASTAGES x A_STAGE_BYTES
-    const uint32_t pring = aring + ARING_BYTES;         // PSTAGES x PI_STAGE_BYTES
+    const uint32_t aring = base + DRING_BYTES;          // ASTAGES x A_SLOT_BYTES
+    const uint32_t pring = aring + ARING_BYTES;         // PSTAGES x PI_SLOT_BYTES
     const uint32_t bar_base = pring + PRING_BYTES;
     uint64_t* bars = (uint64_t*)(base_ptr + DRING_BYTES + ARING_BYTES + PRING_BYTES);
     // bars: data full / empty [D], copy full / empty [A], Pi full / empty [P]; then the accumulator-ready barrier,
@@ -273,13 +283,14 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(pr));
             }
         }
-        // the CTA may not finish while a load it issued is still landing in its shared memory
+        // the CTA may not finish while a load it issued is still landing in its shared memory (even after an abort)
         for (int it = max(0, issued - DSTAGES); it < issued; ++it)
-            mbar_wait_for(dfull_bar(it % DSTAGES), (uint32_t)(it / DSTAGES) & 1u, abort_flag, args.wait_ns);
+            mbar_wait_landed(dfull_bar(it % DSTAGES), (uint32_t)(it / DSTAGES) & 1u, args.wait_ns);
     } else if (warp == 2) {
-        // ---------------- Pi producer: Pi tiles into the main ring once the MMA has released the stage
+        // ---------------- Pi producer: Pi tiles into the ring once the MMA has released the slot (splitting a stage's
+        // two boxes over two issuing warps measured slower: 0.54 against 0.50 ms per 65,536 x 4,000 block)
         if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_pi) : "memory");
-        const uint32_t bytes = args.nh * PI_BOX_BYTES;
+        const uint32_t bytes = (uint32_t)(args.nh * args.pbox * G::ROWB);
         const uint64_t pol_pi = policy_evict_last();
         int issued = 0;
         for (int it = 0; it < n_it; ++it) {
@@ -299,14 +310,15 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
                 mbar_arrive_expect_tx(pfull_bar(s), bytes);
                 const int t = stage_row(it);
                 for (int h = 0; h < args.nh; ++h)
-                    tma_load_2d_hint(pring + s * PI_STAGE_BYTES + h * PI_BOX_BYTES, &tm_pi, t, h * PI_BOX_ROWS,
+                    tma_load_2d_hint(pring + s * PI_SLOT_BYTES + h * PI_BOX_BYTES, &tm_pi, t, h * PI_BOX_ROWS,
                                      pfull_bar(s), pol_pi);
             }
             issued = it + 1;
             __syncwarp();
         }
+        // the CTA may not finish while a load it issued is still landing (even after an abort)
         for (int it = max(0, issued - PSTAGES); it < issued; ++it)
-            mbar_wait_for(pfull_bar(it % PSTAGES), (uint32_t)(it / PSTAGES) & 1u, abort_flag, args.wait_ns);
+            mbar_wait_landed(pfull_bar(it % PSTAGES), (uint32_t)(it / PSTAGES) & 1u, args.wait_ns);
     } else if (warp == 1) {
         // ---------------- MMA issuer (the whole warp waits; lane 0 issues)
         const uint32_t id_full = B16 ? idesc_bf16(TILE_M, PI_BOX_ROWS, false) : idesc_tf32(TILE_M, PI_BOX_ROWS);
@@ -326,14 +338,14 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
             }
             tc_fence_after();
             if (lane == 0) {
-                const uint32_t abase = aring + sa * A_STAGE_BYTES, pbase = pring + sp * PI_STAGE_BYTES;
+                const uint32_t abase = aring + sa * A_SLOT_BYTES, pbase = pring + sp * PI_SLOT_BYTES;
 #pragma unroll
-                for (int kb = 0; kb < 2; ++kb) {
-                    // both operands K-major, 64B swizzle: rows of 64 B, 8-row groups 512 B apart (SBO), K slice
-                    // (8 TF32 or 16 BF16 values) at +32 B
-                    const uint64_t ad = smem_desc(abase + kb * 32, 16, 512, SWZ_64B);
+                for (int kb = 0; kb < G::KSLICES; ++kb) {
+                    // both operands K-major and swizzled (TF32: 128-byte rows, BF16: 64-byte rows; 8-row groups SBO
+                    // apart); K slice kb (8 TF32 or 16 BF16 values) at +32 kb bytes of the row
+                    const uint64_t ad = smem_desc(abase + kb * 32, 16, G::SBO, G::SWZ);
                     for (int h = 0; h < args.nh; ++h) {
-                        const uint64_t bd = smem_desc(pbase + h * PI_BOX_BYTES + kb * 32, 16, 512, SWZ_64B);
+                        const uint64_t bd = smem_desc(pbase + h * PI_BOX_BYTES + kb * 32, 16, G::SBO, G::SWZ);
                         if (B16)
                             mma_bf16(tmem + h * PI_BOX_ROWS, ad, bd, h == args.nh - 1 ? id_last : id_full,
                                      (it > 0 || kb > 0) ? 1u : 0u);
@@ -351,8 +363,8 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
         if (lane == 0) mma_commit(acc_bar);
         __syncwarp();
     } else if (copy_index(warp) >= 0) {
-        // ---------------- copy warps: a 32-column box and the 8-row groups ci / 4 (+ 2) of the stage: column sums of
-        // squares and the K-major operand copy of their rows (TF32: 16 B per 4 rows; BF16: 16 B per 8 rows)
+        // ---------------- copy warps: a 32-column box and the 8-row groups ci / 4, ci / 4 + 2 of the stage: column sums
+        // of squares and the K-major operand copy of their rows (TF32: 16 B per 4 rows; BF16: 16 B per 8 rows)
         const int ci = copy_index(warp);
         const int box = ci & 3, grp0 = ci >> 2;
         const int m = box * 32 + lane;   // data column within the tile
@@ -383,9 +395,10 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(dempty_bar(d));   // staging read: the producer may refill it
-            // K-major copy: data column m is row m (64 B); the 64B swizzle puts chunk q at q ^ ((m >> 1) & 3)
-            uint4* arow = (uint4*)(base_ptr + DRING_BYTES + s * A_STAGE_BYTES + m * 64);
-            const int sw = (m >> 1) & 3;
+            // K-major copy: data column m is operand row m (ROWB bytes); the swizzle puts 16-byte chunk q at q ^ sw
+            // (128-byte rows: sw = m % 8; 64-byte rows: sw = (m / 2) % 4)
+            uint4* arow = (uint4*)(base_ptr + DRING_BYTES + s * A_SLOT_BYTES + m * G::ROWB);
+            const int sw = G::ROWB == 128 ? m & 7 : (m >> 1) & 3;
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
 #pragma unroll
@@ -398,8 +411,8 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
                     v.z = bf16_pair(x[g][4], x[g][5]);
                     v.w = bf16_pair(x[g][6], x[g][7]);
                     arow[gg ^ sw] = v;
-                } else {     // rows 8 grp0 .. 8 grp0 + 7 as TF32 in chunks 2 grp0, 2 grp0 + 1
-                    const int q0 = 2 * grp0;
+                } else {     // rows 8 gg .. 8 gg + 7 as TF32 in chunks 2 gg, 2 gg + 1
+                    const int q0 = 2 * (grp0 + 2 * g);
                     arow[q0 ^ sw] = make_uint4(tf32_bits(x[g][0]), tf32_bits(x[g][1]), tf32_bits(x[g][2]),
                                                tf32_bits(x[g][3]));
                     arow[(q0 + 1) ^ sw] = make_uint4(tf32_bits(x[g][4]), tf32_bits(x[g][5]), tf32_bits(x[g][6]),
@@ -475,6 +488,11 @@ __global__ void __launch_bounds__(THREADS, 1) sketch_tc_kernel(const __grid_cons
 // ------------------------------------------------------------------------------------------------ host side
 bool aligned16(const void* p, int64_t ld) { return ((uintptr_t)p % 16 == 0) && (ld % 4 == 0); }
 
+template <typename K>
+cudaError_t set_smem(K* kernel, int bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 // Pi buffers, side stream and events of the tensor-core engine (created on first use).
 cudaError_t ensure_pi_buffers(smp_ctx* c, size_t bytes) {
     if (!c->gen_stream) {
@@ -540,7 +558,10 @@ cudaError_t generate_pi(smp_ctx* c, int b, int64_t row0, int64_t nrows) {
 
 PiGeom pi_geom(const smp_ctx* c) {
     PiGeom g;
-    g.kpad = (int)round_up(round_up(c->p.k, 16), 256);
+    // binary32 row blocks go to sketch_tc_kernel, whose Pi box is round_up(k, 16) rows when that is at most 256;
+    // the BF16-input engines read 256-row boxes
+    const int k16 = (int)round_up(c->p.k, 16);
+    g.kpad = (c->p.dtype == SMP_F32 && k16 <= PI_BOX_ROWS) ? k16 : (int)round_up(k16, 256);
     g.ld = round_up(c->max_rows, PI_ROW_PAD);
     g.esize = c->p.engine == SMP_ENGINE_TC_FP8 ? 1
               : (c->p.dtype == SMP_BF16 || c->p.engine == SMP_ENGINE_TC_BF16) ? 2 : 4;
@@ -648,20 +669,28 @@ cudaError_t launch_sketch_tc_pi(smp_ctx* c, const void* A, int64_t lda, const vo
                                 int64_t nrows, const float* Pi, int64_t ldp) {
     // SMP_ENGINE_TC_BF16: BF16 operands (32 rows per stage, Pi in BF16); otherwise TF32 operands
     const bool b16 = c->p.engine == SMP_ENGINE_TC_BF16;
-    static std::atomic<bool> attr[2] = {{false}, {false}};
-    if (!attr[b16]) {
-        cudaError_t e = cudaFuncSetAttribute(b16 ? sketch_tc_kernel<true> : sketch_tc_kernel<false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             b16 ? Geo<true>::SMEM_BYTES : Geo<false>::SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        attr[b16] = true;
-    }
-    const int ks = b16 ? Geo<true>::KS : Geo<false>::KS;
     const int k = c->p.k;
     const int kc = (int)round_up(k, 32);                 // TMEM columns drained (multiple of 32)
     const int kmma = (int)round_up(k, 16);               // MMA N coverage
     const int nh = (kmma + PI_BOX_ROWS - 1) / PI_BOX_ROWS;
     const int n_last = kmma - (nh - 1) * PI_BOX_ROWS;
+    const int pbox = nh == 1 ? kmma : PI_BOX_ROWS;
+    const bool small = kmma <= SMALL_KC;
+    const int variant = (b16 ? 1 : 0) + (small ? 2 : 0);
+    static std::atomic<bool> attr[4] = {{false}, {false}, {false}, {false}};
+    if (!attr[variant]) {
+        cudaError_t e = cudaSuccess;
+        switch (variant) {
+            case 0: e = set_smem(sketch_tc_kernel<false, false>, Geo<false, false>::SMEM_BYTES); break;
+            case 1: e = set_smem(sketch_tc_kernel<true, false>, Geo<true, false>::SMEM_BYTES); break;
+            case 2: e = set_smem(sketch_tc_kernel<false, true>, Geo<false, true>::SMEM_BYTES); break;
+            default: e = set_smem(sketch_tc_kernel<true, true>, Geo<true, true>::SMEM_BYTES); break;
+        }
+        if (e != cudaSuccess) return e;
+        attr[variant] = true;
+    }
+    const int ks = (b16 || small) ? 32 : 16;
+    const CUtensorMapSwizzle pi_swz = (!b16 && small) ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
     const int64_t tpad = round_up(nrows, ks);
     cudaStream_t st = c->stream;
     const void* pi = Pi;
@@ -684,14 +713,13 @@ cudaError_t launch_sketch_tc_pi(smp_ctx* c, const void* A, int64_t lda, const vo
     const void* Bp = c->p.same_ab ? A : B;
     const int64_t n2 = c->p.same_ab ? 0 : c->p.n2;
     // data boxes: 128 columns x ks rows, no swizzle = the kernel's DATA_STAGE_BYTES per stage (its expect_tx);
-    // Pi boxes: 64-byte rows (16 TF32 or 32 BF16 values) x 256 sketch rows
+    // Pi boxes: ks values per sketch row (TF32: 128 B, 128-byte swizzle; BF16: 64 B, 64-byte swizzle) x pbox rows
     if (!make_map(&ma, A, (uint64_t)c->p.n1, (uint64_t)nrows, (uint64_t)lda, TILE_M, ks, CU_TENSOR_MAP_SWIZZLE_NONE) ||
         !make_map(&mb, Bp, (uint64_t)(c->p.same_ab ? c->p.n1 : c->p.n2), (uint64_t)nrows,
                   (uint64_t)(c->p.same_ab ? lda : ldb), TILE_M, ks, CU_TENSOR_MAP_SWIZZLE_NONE) ||
-        !(b16 ? make_map(&mp, pi, (uint64_t)pi_inner, (uint64_t)pi_rows, (uint64_t)pld, ks, PI_BOX_ROWS,
+        !(b16 ? make_map(&mp, pi, (uint64_t)pi_inner, (uint64_t)pi_rows, (uint64_t)pld, ks, pbox,
                          CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2)
-              : make_map(&mp, pi, (uint64_t)pi_inner, (uint64_t)pi_rows, (uint64_t)pld, ks, PI_BOX_ROWS,
-                         CU_TENSOR_MAP_SWIZZLE_64B)))
+              : make_map(&mp, pi, (uint64_t)pi_inner, (uint64_t)pi_rows, (uint64_t)pld, ks, pbox, pi_swz)))
         return cudaErrorInvalidValue;
     TcArgs a;
     a.n1 = c->p.n1;
@@ -703,6 +731,7 @@ cudaError_t launch_sketch_tc_pi(smp_ctx* c, const void* A, int64_t lda, const vo
     a.kc = kc;
     a.nh = nh;
     a.n_last = n_last;
+    a.pbox = pbox;
     uint32_t cols = 32;
     while ((int)cols < kc) cols <<= 1;
     a.tmem_cols = cols;
@@ -719,8 +748,12 @@ cudaError_t launch_sketch_tc_pi(smp_ctx* c, const void* A, int64_t lda, const vo
     a.wait_ns = wait > 0 ? (unsigned long long)wait : WAIT_NS;
     a.skip_stage = g_tc_skip_stage.exchange(-1, std::memory_order_relaxed);
     const dim3 grid = smp::counted(dim3((unsigned)tiles, (unsigned)splits));
-    if (b16) sketch_tc_kernel<true><<<grid, THREADS, Geo<true>::SMEM_BYTES, st>>>(ma, mb, mp, a);
-    else sketch_tc_kernel<false><<<grid, THREADS, Geo<false>::SMEM_BYTES, st>>>(ma, mb, mp, a);
+    switch (variant) {
+        case 0: sketch_tc_kernel<false, false><<<grid, THREADS, Geo<false, false>::SMEM_BYTES, st>>>(ma, mb, mp, a); break;
+        case 1: sketch_tc_kernel<true, false><<<grid, THREADS, Geo<true, false>::SMEM_BYTES, st>>>(ma, mb, mp, a); break;
+        case 2: sketch_tc_kernel<false, true><<<grid, THREADS, Geo<false, true>::SMEM_BYTES, st>>>(ma, mb, mp, a); break;
+        default: sketch_tc_kernel<true, true><<<grid, THREADS, Geo<true, true>::SMEM_BYTES, st>>>(ma, mb, mp, a); break;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || buf < 0) return e;
     if (Pi) {   // a caller's Pi: the buffer only becomes free again, nothing is generated ahead

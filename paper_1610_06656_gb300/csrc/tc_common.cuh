@@ -85,6 +85,17 @@ __device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, vol
     }
 }
 
+// Wait until the loads a producer issued into a slot have landed, ignoring the abort flag (a CTA must not exit with
+// a copy into its shared memory in flight); bounded all the same.
+__device__ __forceinline__ bool mbar_wait_landed(uint32_t bar, uint32_t parity, unsigned long long limit_ns) {
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = global_timer();
+    for (;;) {
+        if (mbar_test(bar, parity)) return true;
+        if (global_timer() - t0 > limit_ns) return false;
+    }
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
