@@ -34,6 +34,9 @@ WORKLOADS = {
     "tiny": dict(d=2000, n1=200, n2=200, L=10, sigma=0.1, alpha=0.5, k=100, r=5, T=10, block=65536),
     # one 65,536-row block of the scale shape (1 GB of inputs): the case the ncu captures of the sketch kernel use
     "block": dict(d=65536, n1=2000, n2=2000, L=20, sigma=0.1, alpha=0.5, k=500, r=10, T=10, block=65536),
+    # one 65,536-row block at the largest width and smallest sketch of the batched form (n = 2,048, r = 5, k = 40):
+    # the sketch instantiation for k <= 160 (32-row stages), HBM-bound
+    "block_batch": dict(d=65536, n1=2048, n2=2048, L=20, sigma=0.1, alpha=0.5, k=40, r=5, T=10, block=65536),
     # serving form: Poisson arrivals, job sizes of the batched config (n in [64, 2048], d in [1e4, 5e5],
     # r in {5, 10, 20}, k = 8 r), BF16 inputs windowed from a resident pool, 32,768-row blocks, 120 GB budget
     "serve": dict(rate=200.0, jobs=800, warm_jobs=40, block=32768, pool_rows=1_000_000, width=2048, L=20,
@@ -382,6 +385,10 @@ def main():
     elif b16ops:
         roof = {"bound": "tensor", "achieved": sk_flops / sk_avg_s / 1e12, "peak": peaks["bf16_tflops"],
                 "unit": "TFLOP/s", "peak_kind": "%s bf16 burst" % peak_kind}
+    elif tc_used and sk_flops / sk_bytes * peaks["hbm_gbs"] / 1e3 < peaks["bf16_tflops"] * (1.1 / 2.25):
+        # k / 2 flop per input byte below the TF32 ridge: the HBM stream is the roofline
+        roof = {"bound": "hbm", "achieved": sk_bytes / sk_avg_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "peak_kind": "%s HBM copy" % peak_kind}
     elif tc_used:
         tf32_peak = peaks["bf16_tflops"] * (1.1 / 2.25)
         roof = {"bound": "tensor", "achieved": sk_flops / sk_avg_s / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
@@ -392,7 +399,7 @@ def main():
         roof = {"bound": "alu", "achieved": sk_flops / sk_avg_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
                 "peak_kind": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x %.0f MHz" % clk_mhz}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = sketch_traffic(sum(sk_rows) / len(sk_rows)) if tc_used and not b16ops else None
+    roof["traffic"] = sketch_traffic(sum(sk_rows) / len(sk_rows), w) if tc_used and not b16ops else None
     roof["kernel"] = ("smp_sketch_accumulate: block SRHT (srht_fused_kernel)" if srht else
                       "smp_sketch_accumulate: sketch_tc_kernel<BF16 operands> (tcgen05 kind::f16), Pi of the next "
                       "block generated on a side stream meanwhile" if b16ops else
@@ -970,19 +977,22 @@ def run_batched(args, w, embed=False):
     print(json.dumps(line), flush=True)
 
 
-def sketch_traffic(rows_per_launch):
-    """DRAM bytes (read + write) per sketch launch from the committed ncu capture of sketch_tc_kernel, scaled to the
-    rows one launch of this run processes; None when the kernel source has changed since the capture."""
+def sketch_traffic(rows_per_launch, w):
+    """DRAM bytes (read + write) per sketch launch from the committed ncu capture of sketch_tc_kernel of the same
+    instantiation and width (k <= 160: the n = 2,048, k = 40 block; otherwise the n = 2,000, k = 500 block), scaled
+    to the rows one launch of this run processes; None when the kernel source has changed since the capture or no
+    capture matches the shape."""
     import hashlib
+    name = "sketch_tc_small_block.md" if w["k"] <= 160 else "sketch_tc_full_scale.md"
     try:
-        with open(os.path.join(ROOT, "profiles", "sketch_tc_full_scale.md")) as f:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
             line = next(ln for ln in f if ln.startswith("bench: "))
         kv = dict(tok.split("=") for tok in line.split()[1:])
         with open(os.path.join(ROOT, "paper_1610_06656_gb300", "csrc", "sketch_tc.cu"), "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()[:16]
     except (OSError, StopIteration, ValueError):
         return None
-    if kv.get("sha") != sha:
+    if kv.get("sha") != sha or int(kv.get("ntot", -1)) != w["n1"] + w["n2"]:
         return None
     return float(kv["traffic_bytes"]) * rows_per_launch / float(kv["rows"])
 
