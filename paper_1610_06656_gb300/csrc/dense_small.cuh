@@ -52,46 +52,59 @@ __global__ void gram_reduce_kernel(const double* __restrict__ part, int nblk, in
     if (lane == 0) G[pq] = s;
 }
 
-// Upper Cholesky factor R (G = R^T R) of a b x b symmetric matrix by one warp. A pivot <= tol * max diag marks a
-// rank-deficient direction: that row of R is zeroed (apply_rinv then zeroes the column).
-__global__ void chol_kernel(const double* __restrict__ G, int b, double* R, double tol) {
+// Upper Cholesky factor R (G = R^T R, R row-major b x b) of a b x b symmetric matrix, 32 < b <= MAX_SMALL. A pivot
+// <= tol * max diag marks a rank-deficient direction: that row of R is zeroed (apply_rinv then zeroes the column).
+// Four warps: one thread takes each pivot; the column scaling and the trailing update's (i, k) pairs are spread over
+// all 128 threads, so the binary64 work lands on the SM's four sub-partitions (one warp alone: 0.15 ms at b = 48).
+__global__ void __launch_bounds__(128) chol_par_kernel(const double* __restrict__ G, int b, double* R, double tol) {
     __shared__ double L[MAX_SMALL][MAX_SMALL + 1];
-    __shared__ double rinv_j;
-    const int lane = threadIdx.x;
-    double maxd = 0.0;
-    for (int e = lane; e < b * b; e += 32) {
+    __shared__ double rinv_j, maxd_s;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < b * b; e += 128) {
         const int i = e / b, j = e - i * b;
         L[i][j] = G[e];
-        if (i == j) maxd = fmax(maxd, G[e]);
     }
+    __syncthreads();
+    if (tid < 32) {
+        double maxd = 0.0;
+        for (int i = tid; i < b; i += 32) maxd = fmax(maxd, L[i][i]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) maxd = fmax(maxd, __shfl_xor_sync(0xffffffffu, maxd, o));
-    __syncwarp();
+        for (int o = 16; o > 0; o >>= 1) maxd = fmax(maxd, __shfl_xor_sync(0xffffffffu, maxd, o));
+        if (tid == 0) maxd_s = maxd;
+    }
+    __syncthreads();
+    const double maxd = maxd_s;
     for (int j = 0; j < b; ++j) {
-        if (lane == 0) {
+        if (tid == 0) {
             const double d = L[j][j];
             const bool ok = d > tol * maxd && d > 0.0;
             const double y = ok ? rsqrt_refined(d) : 0.0;
             L[j][j] = ok ? d * y : 0.0;
             rinv_j = y;
         }
-        __syncwarp();
+        __syncthreads();
         const double y = rinv_j;
-        for (int i = j + 1 + lane; i < b; i += 32) L[i][j] *= y;
-        __syncwarp();
-        for (int i = j + 1 + lane; i < b; i += 32) {
-            const double lij = L[i][j];
-            for (int kk = j + 1; kk <= i; ++kk) L[i][kk] -= lij * L[kk][j];
+        for (int i = j + 1 + tid; i < b; i += 128) L[i][j] *= y;
+        __syncthreads();
+        // pairs (i, k), j < k <= i < b, numbered p = a (a + 1) / 2 + c with i = j + 1 + a, k = j + 1 + c
+        const int m = b - j - 1;
+        const int np = m * (m + 1) / 2;
+        for (int p = tid; p < np; p += 128) {
+            int a = (int)((sqrtf(8.f * (float)p + 1.f) - 1.f) * 0.5f);
+            if ((a + 1) * (a + 2) / 2 <= p) ++a;
+            if (a * (a + 1) / 2 > p) --a;
+            const int i = j + 1 + a, k = j + 1 + (p - a * (a + 1) / 2);
+            L[i][k] = fma(-L[i][j], L[k][j], L[i][k]);
         }
-        __syncwarp();
+        __syncthreads();
     }
-    for (int e = lane; e < b * b; e += 32) {
+    for (int e = tid; e < b * b; e += 128) {
         const int i = e / b, j = e - i * b;
         R[e] = j >= i ? L[j][i] : 0.0;
     }
 }
 
-// Upper Cholesky factor of a b x b symmetric matrix (b <= 32), same pivot rule and output as chol_kernel, on four
+// Upper Cholesky factor of a b x b symmetric matrix (b <= 32), same pivot rule and output as chol_par_kernel, on four
 // warps: every warp keeps the whole matrix in registers (lane i holds row i), computes each pivot and its column
 // (in parallel, identically), and updates only the trailing columns kk with kk % 4 == its warp id, so the binary64
 // work of the trailing updates is spread over the SM's four sub-partitions (on this part each issues about one

@@ -280,108 +280,133 @@ __global__ void __launch_bounds__(32 * LS_WARPS) seg_gram_kernel(
     }
 }
 
-// Gc[o] = sum of the segment partials of output row o, in segment order and in binary64: the packed lower triangle
-// of G (r (r + 1) / 2 values) followed by b (r values). One warp per row; lanes over the r^2 + r partial values,
-// so every segment is read with coalesced loads.
-template <typename TG>
+// Gc[o] (binary64) = sum of the segment partials of output row o, in segment order and in the partials' type (binary32
+// partials summed in binary32, as the lane path for r <= 12 does: binary64 arithmetic, conversions included, issues
+// about one warp instruction per 64 cycles per SM sub-partition here, and summing binary32 partials in it took
+// 70 us at n = 1,504, r = 20): the packed lower triangle of G (r (r + 1) / 2 values) followed by b (r values). One
+// warp per row; lanes over the r^2 + r partial values (every segment read with coalesced loads).
+template <typename TG, int RMAX>
 __global__ void __launch_bounds__(256) seg_reduce_kernel(const int64_t* __restrict__ seg_start,
                                                          const TG* __restrict__ part, int r, int64_t n_out,
                                                          double* Gc) {
+    constexpr int Q = (RMAX * RMAX + RMAX + 31) / 32;
     const int64_t o = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (o >= n_out) return;
     const int stride = r * r + r;
     const int nt = r * (r + 1) / 2;
     double* dst = Gc + o * (int64_t)(nt + r);
-    for (int e0 = 0; e0 < stride; e0 += 32) {
-        const int e = e0 + lane;
-        double acc = 0.0;
-        if (e < stride)
-            for (int64_t s = seg_start[o]; s < seg_start[o + 1]; ++s) acc += (double)part[s * (int64_t)stride + e];
+    TG acc[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) acc[q] = TG(0);
+    // four segments' values are loaded before they are added (in segment order): rows with many samples (the
+    // large-norm rows get most of them) have dozens of segments, and a round trip per segment made them the tail
+    const int64_t s0 = seg_start[o], s1 = seg_start[o + 1];
+    for (int64_t sg = s0; sg < s1; sg += 4) {
+        TG v[4][Q];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const TG* ps = part + (sg + u) * (int64_t)stride;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int e = q * 32 + lane;
+                v[u][q] = (sg + u < s1 && e < stride) ? ps[e] : TG(0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+                if (sg + u < s1) acc[q] += v[u][q];
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int e = q * 32 + lane;
         if (e < r * r) {
             const int i = e / r, j = e - i * r;
-            if (j <= i) dst[i * (i + 1) / 2 + j] = acc;
+            if (j <= i) dst[i * (i + 1) / 2 + j] = (double)acc[q];
         } else if (e < stride) {
-            dst[nt + (e - r * r)] = acc;
+            dst[nt + (e - r * r)] = (double)acc[q];
         }
     }
 }
 
-// One thread per output row (32 rows per CTA): ridge, Cholesky and solve of its compact binary64 system. The 32
-// systems are first staged into shared memory as [element][lane] with coalesced loads, so every later access is
-// conflict-free and nothing spills to local memory.
-template <typename TF, int RMAX>
-__global__ void __launch_bounds__(32) solve_kernel(const double* __restrict__ Gc, int r, int64_t n_out, TF* Xout,
-                                                   int* err) {
-    constexpr int NT = RMAX * (RMAX + 1) / 2;
-    extern __shared__ double solve_sm[];
-    const int lane = threadIdx.x;
-    double* Ls = solve_sm;               // [NT][32]
-    double* ys = solve_sm + NT * 32;     // [RMAX][32]
-    double* ri = ys + RMAX * 32;         // [RMAX][32]
-#define LL(e) Ls[(e) * 32 + lane]
-#define YY(i) ys[(i) * 32 + lane]
-#define RI(i) ri[(i) * 32 + lane]
-    const int nt = r * (r + 1) / 2;
-    const int64_t o0 = (int64_t)blockIdx.x * 32;
-    for (int q = 0; q < 32 && o0 + q < n_out; ++q) {
-        const double* src = Gc + (o0 + q) * (int64_t)(nt + r);
-        for (int e = lane; e < nt + r; e += 32) {
-            if (e < nt) Ls[e * 32 + q] = src[e];
-            else ys[(e - nt) * 32 + q] = src[e];
-        }
-    }
+// Ridge, Cholesky and solve of each output row's compact binary64 system with one warp per row (r <= 32), for the
+// orders where one thread per row is too long a binary64 chain: binary64 issues about one warp instruction per 64
+// cycles per SM sub-partition, so a row per thread puts r^3 / 6 dependent instructions on one warp of every 32 rows
+// (47 warps for n = 1,504 at r = 20: 0.18 ms), while a warp per row spreads the factorisation over every
+// sub-partition. The factorisation is
+// right-looking: lane 0 takes the pivot, the lanes scale the column below it and then share the trailing update's
+// (i, k) pairs; the substitutions keep y[i] in lane i and broadcast each solved entry. Eight rows per CTA, each with
+// its packed triangle in shared memory.
+template <typename TF>
+__global__ void __launch_bounds__(256) solve_warp_kernel(const double* __restrict__ Gc, int r, int64_t n_out,
+                                                         TF* Xout, int* err) {
+    constexpr int W = 8;
+    __shared__ double Lsm[W][32 * 33 / 2];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t o = (int64_t)blockIdx.x * W + w;
+    if (o >= n_out) return;   // warp-uniform
+    double* L = Lsm[w];
+    auto T = [](int i) { return i * (i + 1) / 2; };
+    const int nt = T(r);
+    const double* src = Gc + o * (int64_t)(nt + r);
+    for (int e = lane; e < nt; e += 32) L[e] = src[e];
+    double y = lane < r ? src[nt + lane] : 0.0;
     __syncwarp();
-    const int64_t o = o0 + lane;
-    if (o >= n_out) return;
-    double tr = 0.0;
-    for (int i = 0; i < r; ++i) tr += LL(i * (i + 1) / 2 + i);
+    double tr = lane < r ? L[T(lane) + lane] : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, off);
     if (!(tr > 0.0)) {
-        for (int i = 0; i < r; ++i) Xout[o * r + i] = TF(0);
+        if (lane < r) Xout[o * r + lane] = TF(0);
         return;
     }
     const double lam = 1e-10 * tr / (double)r;
-    for (int i = 0; i < r; ++i) LL(i * (i + 1) / 2 + i) += lam;
+    if (lane < r) L[T(lane) + lane] += lam;
+    __syncwarp();
+    double rj_mine = 0.0;   // lane j keeps 1 / L[j][j]
     for (int j = 0; j < r; ++j) {
-        const int jb = j * (j + 1) / 2;
-        double d = LL(jb + j);
-        for (int k = 0; k < j; ++k) d -= LL(jb + k) * LL(jb + k);
+        const double d = L[T(j) + j];   // the same value in every lane: the branch below is warp-uniform
         if (!(d > 0.0)) {
-            set_error(err, DEVERR_NUMERIC);
-            for (int i = 0; i < r; ++i) Xout[o * r + i] = TF(0);
+            if (lane == 0) set_error(err, DEVERR_NUMERIC);
+            if (lane < r) Xout[o * r + lane] = TF(0);
             return;
         }
         const double rj = rsqrt_refined(d);
-        RI(j) = rj;
-        LL(jb + j) = d * rj;
-        for (int i = j + 1; i < r; ++i) {
-            const int ib = i * (i + 1) / 2;
-            double v = LL(ib + j);
-            for (int k = 0; k < j; ++k) v -= LL(ib + k) * LL(jb + k);
-            LL(ib + j) = v * rj;
+        if (lane == j) rj_mine = rj;
+        __syncwarp();
+        if (lane == 0) L[T(j) + j] = d * rj;
+        for (int i = j + 1 + lane; i < r; i += 32) L[T(i) + j] *= rj;
+        __syncwarp();
+        // pairs (i, k), j < k <= i < r, numbered p = a (a + 1) / 2 + c with i = j + 1 + a, k = j + 1 + c
+        const int m = r - j - 1;
+        const int np = T(m);
+        for (int p = lane; p < np; p += 32) {
+            int a = (int)((sqrtf(8.f * (float)p + 1.f) - 1.f) * 0.5f);
+            if (T(a + 1) <= p) ++a;
+            if (T(a) > p) --a;
+            const int i = j + 1 + a, k = j + 1 + (p - T(a));
+            L[T(i) + k] = fma(-L[T(i) + j], L[T(k) + j], L[T(i) + k]);
         }
+        __syncwarp();
     }
-    for (int i = 0; i < r; ++i) {   // L z = y
-        const int ib = i * (i + 1) / 2;
-        double v = YY(i);
-        for (int k = 0; k < i; ++k) v -= LL(ib + k) * YY(k);
-        YY(i) = v * RI(i);
+    for (int j = 0; j < r; ++j) {   // L z = y
+        const double zj = __shfl_sync(0xffffffffu, y, j) * __shfl_sync(0xffffffffu, rj_mine, j);
+        if (lane == j) y = zj;
+        else if (lane > j && lane < r) y = fma(-L[T(lane) + j], zj, y);
     }
-    for (int i = r - 1; i >= 0; --i) {   // L^T x = z
-        double v = YY(i);
-        for (int k = i + 1; k < r; ++k) v -= LL(k * (k + 1) / 2 + i) * YY(k);
-        YY(i) = v * RI(i);
+    for (int j = r - 1; j >= 0; --j) {   // L^T x = z
+        const double xj = __shfl_sync(0xffffffffu, y, j) * __shfl_sync(0xffffffffu, rj_mine, j);
+        if (lane == j) y = xj;
+        else if (lane < j) y = fma(-L[T(j) + lane], xj, y);
     }
-    for (int i = 0; i < r; ++i) Xout[o * r + i] = (TF)YY(i);
-#undef LL
-#undef YY
-#undef RI
+    if (lane < r) Xout[o * r + lane] = (TF)y;
 }
 
 // The same ridge + Cholesky solve with each row's system held in registers (r <= R: R (R + 1) / 2 + 2 R doubles).
 // Binary64 on this part issues about one warp instruction per 64 cycles per SM sub-partition whatever the number of
-// active lanes, so a warp's binary64 instruction count sets the time; registers remove the shared-memory round trip
-// the general kernel makes for every operand. Every index is a template constant (the loops are generated by
+// active lanes, so a warp's binary64 instruction count sets the time; registers remove a shared-memory round trip
+// for every operand. Every index is a template constant (the loops are generated by
 // recursion, so no array is indexed at run time and nothing goes to local memory); r only enters warp-uniform guards.
 template <int R>
 struct RegChol {
@@ -505,11 +530,6 @@ __global__ void __launch_bounds__(32) solve_reg_kernel(const double* __restrict_
         if (i < r) Xout[o * r + i] = (TF)y[i];
 }
 
-template <int RMAX>
-constexpr int solve_smem_bytes() {
-    return (RMAX * (RMAX + 1) / 2 + 2 * RMAX) * 32 * 8;
-}
-
 // ---------------------------------------------------------------------------------------------------------------
 // canonical form
 // ---------------------------------------------------------------------------------------------------------------
@@ -616,7 +636,7 @@ void gram_chol(const TX* X, int64_t n, int b, double* part, double* G, double* R
     if (b <= 32)
         chol32_kernel<<<smp::counted(1), 128, 0, st>>>(G, b, R, 1e-28);
     else
-        chol_kernel<<<smp::counted(1), 32, 0, st>>>(G, b, R, 1e-28);
+        chol_par_kernel<<<smp::counted(1), 128, 0, st>>>(G, b, R, 1e-28);
 }
 
 // Xout = Xin R^-1 (registers for b <= 32).
@@ -740,11 +760,30 @@ __global__ void __launch_bounds__(256) seg_reduce_lane_kernel(const int64_t* __r
     const int nt = r * (r + 1) / 2;
     double* dst = Gc + o * (int64_t)(nt + r);
     const int64_t s0 = seg_start[o], s1 = seg_start[o + 1];
-    for (int e = lane; e < LANE_PS; e += 32) {
-        float acc = 0.f;
-        for (int64_t s = s0; s < s1; ++s) acc += part[s * (int64_t)LANE_PS + e];
-        if (e < nt) dst[e] = (double)acc;
-        else if (e >= LANE_NT && e < LANE_NT + r) dst[nt + (e - LANE_NT)] = (double)acc;
+    constexpr int Q = (LANE_PS + 31) / 32;
+    float acc[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) acc[q] = 0.f;
+    for (int64_t s = s0; s < s1; s += 4) {   // four segments' loads in flight, added in segment order
+        float v[4][Q];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int e = q * 32 + lane;
+                v[u][q] = (s + u < s1 && e < LANE_PS) ? part[(s + u) * (int64_t)LANE_PS + e] : 0.f;
+            }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+                if (s + u < s1) acc[q] += v[u][q];
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int e = q * 32 + lane;
+        if (e < nt) dst[e] = (double)acc[q];
+        else if (e >= LANE_NT && e < LANE_NT + r) dst[nt + (e - LANE_NT)] = (double)acc[q];
     }
 }
 
@@ -755,11 +794,7 @@ void launch_ls(int r, const Segments& sg, const int32_t* idx, const int64_t* pos
     const unsigned g = nblocks(sg.nseg, LS_WARPS);
     const unsigned gr = nblocks(n_out * 32, 256);
     const unsigned gs = nblocks(n_out, 32);
-    static std::atomic<bool> attr{false};
-    if (!attr) {
-        cudaFuncSetAttribute(solve_kernel<TF, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, solve_smem_bytes<32>());
-        attr = true;
-    }
+    const unsigned gw = nblocks(n_out, 8);
     if (sizeof(TG) == 4 && r <= LANE_R) {
         seg_gram_lane_kernel<TF, TV><<<smp::counted(g), 32 * LS_WARPS, 0, st>>>(sg.b, sg.e, sg.nseg, idx, pos, vals,
                                                                                 wt, sub, sid, Fin, r, (float*)part);
@@ -768,21 +803,26 @@ void launch_ls(int r, const Segments& sg, const int32_t* idx, const int64_t* pos
     } else if (r <= 8) {
         seg_gram_kernel<TF, TG, TV, 8><<<smp::counted(g), 32 * LS_WARPS, 0, st>>>(sg.b, sg.e, sg.nseg, idx, pos,
                                                                                   vals, qhat, sub, sid, Fin, r, part);
-        seg_reduce_kernel<TG><<<smp::counted(gr), 256, 0, st>>>(sg.start, part, r, n_out, Gc);
+        seg_reduce_kernel<TG, 8><<<smp::counted(gr), 256, 0, st>>>(sg.start, part, r, n_out, Gc);
         solve_reg_kernel<TF, 12><<<smp::counted(gs), 32, 0, st>>>(Gc, r, n_out, Xout, err);
     } else if (r <= 16) {
         seg_gram_kernel<TF, TG, TV, 16><<<smp::counted(g), 32 * LS_WARPS, 0, st>>>(sg.b, sg.e, sg.nseg, idx, pos,
                                                                                    vals, qhat, sub, sid, Fin, r, part);
-        seg_reduce_kernel<TG><<<smp::counted(gr), 256, 0, st>>>(sg.start, part, r, n_out, Gc);
+        seg_reduce_kernel<TG, 16><<<smp::counted(gr), 256, 0, st>>>(sg.start, part, r, n_out, Gc);
         if (r <= 12)
             solve_reg_kernel<TF, 12><<<smp::counted(gs), 32, 0, st>>>(Gc, r, n_out, Xout, err);
         else
-            solve_kernel<TF, 16><<<smp::counted(gs), 32, solve_smem_bytes<16>(), st>>>(Gc, r, n_out, Xout, err);
+            solve_warp_kernel<TF><<<smp::counted(gw), 256, 0, st>>>(Gc, r, n_out, Xout, err);
+    } else if (r <= 20) {
+        seg_gram_kernel<TF, TG, TV, 20><<<smp::counted(g), 32 * LS_WARPS, 0, st>>>(sg.b, sg.e, sg.nseg, idx, pos,
+                                                                                   vals, qhat, sub, sid, Fin, r, part);
+        seg_reduce_kernel<TG, 20><<<smp::counted(gr), 256, 0, st>>>(sg.start, part, r, n_out, Gc);
+        solve_warp_kernel<TF><<<smp::counted(gw), 256, 0, st>>>(Gc, r, n_out, Xout, err);
     } else {
         seg_gram_kernel<TF, TG, TV, 32><<<smp::counted(g), 32 * LS_WARPS, 0, st>>>(sg.b, sg.e, sg.nseg, idx, pos,
                                                                                    vals, qhat, sub, sid, Fin, r, part);
-        seg_reduce_kernel<TG><<<smp::counted(gr), 256, 0, st>>>(sg.start, part, r, n_out, Gc);
-        solve_kernel<TF, 32><<<smp::counted(gs), 32, solve_smem_bytes<32>(), st>>>(Gc, r, n_out, Xout, err);
+        seg_reduce_kernel<TG, 32><<<smp::counted(gr), 256, 0, st>>>(sg.start, part, r, n_out, Gc);
+        solve_warp_kernel<TF><<<smp::counted(gw), 256, 0, st>>>(Gc, r, n_out, Xout, err);
     }
 }
 
