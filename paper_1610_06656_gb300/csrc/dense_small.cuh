@@ -163,73 +163,41 @@ __global__ void __launch_bounds__(128) chol32_kernel(const double* __restrict__ 
     }
 }
 
-// X_out[i] = X_in[i] R^-1 (row vector times inverse upper factor), the substitution carried out in TC (binary32
-// for the subspace iteration's first Cholesky-QR pass, whose second pass restores orthogonality; binary64 for the
-// canonical form); a zero pivot zeroes that column.
-template <typename TIn, typename TOut, typename TC>
+// Xout[i] = Xin[i] R^-1 (row vector times the inverse of the upper factor R, b x b row-major, b <= NB), the
+// substitution carried out in TC (binary32 for the subspace iteration's first Cholesky-QR pass, whose second pass
+// restores orthogonality; binary64 for the canonical form), one thread per row with the row in registers: the substitution's loops are fully
+// unrolled (every index of x is a compile-time constant, so x stays in registers instead of local memory; a run-time
+// index sent it to local memory: 55 us at n = 1,504, b = 48); b only enters warp-uniform guards. R^-1's
+// diagonal comes from rsqrt_refined(d^2), zero where R's diagonal is zero (a rank-deficient direction). Instantiated
+// for b <= 32, 48 and 72; the work is that of NB.
+template <typename TIn, typename TOut, typename TC, int NB>
 __global__ void __launch_bounds__(128) apply_rinv_kernel(const TIn* __restrict__ Xin, int64_t n, int b,
                                                          const double* __restrict__ R, TOut* Xout) {
-    __shared__ TC Rs[MAX_SMALL * MAX_SMALL];
-    __shared__ TC dinv[MAX_SMALL];
-    for (int e = threadIdx.x; e < b * b; e += blockDim.x) Rs[e] = (TC)R[e];
-    for (int j = threadIdx.x; j < b; j += blockDim.x) {
-        const double d = R[j * b + j];
+    // R padded to NB x NB with zeros (and a zero inverse diagonal) beyond b, so the substitution needs no guards
+    __shared__ TC Rs[NB * NB];
+    __shared__ TC dinv[NB];
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int l = e / NB, j = e - l * NB;
+        Rs[e] = (l < b && j < b) ? (TC)R[l * b + j] : TC(0);
+    }
+    for (int j = threadIdx.x; j < NB; j += blockDim.x) {
+        const double d = j < b ? R[j * b + j] : 0.0;
         dinv[j] = d > 0.0 ? (TC)rsqrt_refined(d * d) : TC(0);
     }
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    TC x[MAX_SMALL];
-    for (int j = 0; j < b; ++j) {
-        TC y = (TC)Xin[i * b + j];
-        for (int l = 0; l < j; ++l) y -= x[l] * Rs[l * b + j];
+    const TIn* xin = Xin + i * b;
+    TC x[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        TC y = j < b ? (TC)xin[j] : TC(0);
+#pragma unroll
+        for (int l = 0; l < j; ++l) y -= x[l] * Rs[l * NB + j];
         x[j] = y * dinv[j];
     }
-    for (int j = 0; j < b; ++j) Xout[i * b + j] = (TOut)x[j];
-}
-
-// apply_rinv_kernel for b <= 32 with the row in registers: the substitution is unrolled by template recursion (every
-// index of x is a compile-time constant, so x stays in registers instead of local memory); b only enters
-// warp-uniform guards. R^-1's diagonal comes from rsqrt_refined(d^2) as above.
-template <typename TC>
-struct Rinv32 {
-    template <int J, int L>
-    static __device__ __forceinline__ void dot(const TC* Rs, const TC (&x)[32], int b, TC& y) {
-        if constexpr (L < J) {
-            y -= x[L] * Rs[L * b + J];
-            dot<J, L + 1>(Rs, x, b, y);
-        }
-    }
-    template <int J, typename TIn>
-    static __device__ __forceinline__ void step(const TC* Rs, const TC* dinv, const TIn* xin, TC (&x)[32], int b) {
-        if constexpr (J < 32) {
-            if (J < b) {
-                TC y = (TC)xin[J];
-                dot<J, 0>(Rs, x, b, y);
-                x[J] = y * dinv[J];
-                step<J + 1>(Rs, dinv, xin, x, b);
-            }
-        }
-    }
-};
-
-template <typename TIn, typename TOut, typename TC>
-__global__ void __launch_bounds__(128) apply_rinv32_kernel(const TIn* __restrict__ Xin, int64_t n, int b,
-                                                           const double* __restrict__ R, TOut* Xout) {
-    __shared__ TC Rs[32 * 32];
-    __shared__ TC dinv[32];
-    for (int e = threadIdx.x; e < b * b; e += blockDim.x) Rs[e] = (TC)R[e];
-    for (int j = threadIdx.x; j < b; j += blockDim.x) {
-        const double d = R[j * b + j];
-        dinv[j] = d > 0.0 ? (TC)rsqrt_refined(d * d) : TC(0);
-    }
-    __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    TC x[32];
-    Rinv32<TC>::template step<0>(Rs, dinv, Xin + i * b, x, b);
 #pragma unroll
-    for (int j = 0; j < 32; ++j)
+    for (int j = 0; j < NB; ++j)
         if (j < b) Xout[i * b + j] = (TOut)x[j];
 }
 

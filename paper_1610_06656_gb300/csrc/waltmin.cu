@@ -639,13 +639,16 @@ void gram_chol(const TX* X, int64_t n, int b, double* part, double* G, double* R
         chol_par_kernel<<<smp::counted(1), 128, 0, st>>>(G, b, R, 1e-28);
 }
 
-// Xout = Xin R^-1 (registers for b <= 32).
+// Xout = Xin R^-1 (the row in registers; instantiations for b <= 32, 48 and MAX_SMALL).
 template <typename TIn, typename TOut, typename TC>
 void apply_rinv(const TIn* Xin, int64_t n, int b, const double* R, TOut* Xout, cudaStream_t st) {
+    const unsigned g = smp::counted(nblocks(n, 128));
     if (b <= 32)
-        apply_rinv32_kernel<TIn, TOut, TC><<<smp::counted(nblocks(n, 128)), 128, 0, st>>>(Xin, n, b, R, Xout);
+        apply_rinv_kernel<TIn, TOut, TC, 32><<<g, 128, 0, st>>>(Xin, n, b, R, Xout);
+    else if (b <= 48)
+        apply_rinv_kernel<TIn, TOut, TC, 48><<<g, 128, 0, st>>>(Xin, n, b, R, Xout);
     else
-        apply_rinv_kernel<TIn, TOut, TC><<<smp::counted(nblocks(n, 128)), 128, 0, st>>>(Xin, n, b, R, Xout);
+        apply_rinv_kernel<TIn, TOut, TC, MAX_SMALL><<<g, 128, 0, st>>>(Xin, n, b, R, Xout);
 }
 
 template <typename TX, typename TQ, typename TC>

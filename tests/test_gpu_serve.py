@@ -172,7 +172,8 @@ def test_collect_timeout_and_destroy_with_live_jobs(env):
             for r0, nr in serve.block_plan(j.d, 32768):
                 smp.smp_serve_block(sv, jid, A[j.row_offset + r0:j.row_offset + r0 + nr, :j.n], A.stride(0),
                                     B[j.row_offset + r0:j.row_offset + r0 + nr, :j.n], B.stride(0), r0, nr)
-            smp.smp_serve_close(sv, jid)
+        smp.smp_serve_close(sv, ids[0])              # both closed back to back: job 1 queues behind job 0's chain
+        smp.smp_serve_close(sv, ids[1])
         with pytest.raises(smp.SmpError) as e:       # one worker, two chains of milliseconds each: not done yet
             smp.smp_serve_collect(sv, ids[1], timeout_s=0.0)
         assert e.value.status == smp.SMP_ETIMEOUT
