@@ -696,6 +696,7 @@ void spmm(const Segments& sg, const int32_t* idx, const TY* val, const TY* X, in
 constexpr int LANE_R = 12;
 constexpr int LANE_NT = LANE_R * (LANE_R + 1) / 2;
 constexpr int LANE_PS = (LANE_NT + LANE_R + 3) / 4 * 4;   // floats per segment partial (packed G, then b)
+constexpr int LANE2_PS = (20 * 21 / 2 + 20 + 3) / 4 * 4;  // the same for the two-pass lane path (r <= 20)
 
 // w_e = 1 / q^_e for every sample of Omega (binary32), once per WAltMin call.
 __global__ void weights_kernel(const double* __restrict__ qhat, int64_t nnz, float* wt) {
@@ -752,18 +753,92 @@ __global__ void __launch_bounds__(32 * LS_WARPS) seg_gram_lane_kernel(
     }
 }
 
-// Gc[o] (binary64, the layout solve_reg_kernel reads: packed G of rows < r, then b) = sum of the row's segment
-// partials in segment order, in binary32. One warp per row, lanes over the partial's values.
+// The lane Gram path for 12 < r <= R (R = 20): one sample per lane as in seg_gram_lane_kernel, the packed triangle
+// split over two passes over the segment's samples so each pass's accumulators fit in registers (pass 0: rows
+// [0, RS); pass 1: rows [RS, R) and b). Against one warp per segment broadcasting each sample's factor row with
+// shuffles (RMAX shuffles and FMAs per sample and lane), about a fifth of the instructions. Layout of a partial:
+// G(a, c) at a (a + 1) / 2 + c, b(a) at R (R + 1) / 2 + a, zeros beyond r.
+template <typename TF, typename TV, int R, int RS>
+__global__ void __launch_bounds__(32 * LS_WARPS) seg_gram_lane2_kernel(
+    const int64_t* __restrict__ seg_b, const int64_t* __restrict__ seg_e, int64_t nseg,
+    const int32_t* __restrict__ idx, const int64_t* __restrict__ pos, const TV* __restrict__ vals,
+    const float* __restrict__ wt, const uint8_t* __restrict__ sub, int sid, const TF* __restrict__ Fin, int r,
+    float* part) {
+    constexpr int NT = R * (R + 1) / 2;
+    constexpr int PS = (NT + R + 3) / 4 * 4;
+    constexpr int N0 = RS * (RS + 1) / 2;      // pass 0 values
+    constexpr int N1 = NT - N0 + R;            // pass 1 values (rows RS.. of G, then b)
+    constexpr int NA = N0 > N1 ? N0 : N1;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t s = (int64_t)blockIdx.x * LS_WARPS + wid;
+    if (s >= nseg) return;
+    const int64_t p1 = seg_e[s];
+    float* dst = part + s * (int64_t)PS;
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+        float g[NA];
+#pragma unroll
+        for (int e = 0; e < NA; ++e) g[e] = 0.f;
+        for (int64_t p = seg_b[s] + lane; p < p1; p += 32) {
+            const int64_t e = pos ? pos[p] : p;
+            if (sub != nullptr && sub[e] != sid) continue;
+            const float w = wt[e];
+            const TF* fr = Fin + (int64_t)idx[p] * r;
+            float f[R];
+#pragma unroll
+            for (int a = 0; a < R; ++a) f[a] = a < r ? (float)fr[a] : 0.f;
+            if (pass == 0) {
+#pragma unroll
+                for (int a = 0; a < RS; ++a) {
+                    const float wf = w * f[a];
+#pragma unroll
+                    for (int c = 0; c <= a; ++c) g[a * (a + 1) / 2 + c] = fmaf(wf, f[c], g[a * (a + 1) / 2 + c]);
+                }
+            } else {
+                const float wm = w * (float)vals[e];
+#pragma unroll
+                for (int a = RS; a < R; ++a) {
+                    const float wf = w * f[a];
+#pragma unroll
+                    for (int c = 0; c <= a; ++c)
+                        g[a * (a + 1) / 2 - N0 + c] = fmaf(wf, f[c], g[a * (a + 1) / 2 - N0 + c]);
+                }
+#pragma unroll
+                for (int a = 0; a < R; ++a) g[NT - N0 + a] = fmaf(wm, f[a], g[NT - N0 + a]);
+            }
+        }
+        const int nv = pass == 0 ? N0 : N1, off = pass == 0 ? 0 : N0;
+#pragma unroll
+        for (int c0 = 0; c0 < NA; c0 += 32) {
+            if (c0 < nv) {
+                float v[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) v[i] = (c0 + i < NA && c0 + i < nv) ? g[c0 + i] : 0.f;
+                const float tot = transpose_sum32(v, lane);
+                if (c0 + lane < nv) dst[off + c0 + lane] = tot;
+            }
+        }
+    }
+    static_assert(R != 20 || PS == LANE2_PS, "partial size");
+    if (lane < PS - NT - R) dst[NT + R + lane] = 0.f;   // padding
+}
+
+// Gc[o] (binary64, the layout the solves read: packed G of rows < r, then b) = sum of the row's segment partials
+// of the lane Gram paths (R = LANE_R or 20), in segment order, in binary32. One warp per row, lanes over the
+// partial's values.
+template <int R>
 __global__ void __launch_bounds__(256) seg_reduce_lane_kernel(const int64_t* __restrict__ seg_start,
                                                               const float* __restrict__ part, int r, int64_t n_out,
                                                               double* Gc) {
+    constexpr int NTR = R * (R + 1) / 2;
+    constexpr int PSR = (NTR + R + 3) / 4 * 4;
     const int64_t o = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (o >= n_out) return;
     const int nt = r * (r + 1) / 2;
     double* dst = Gc + o * (int64_t)(nt + r);
     const int64_t s0 = seg_start[o], s1 = seg_start[o + 1];
-    constexpr int Q = (LANE_PS + 31) / 32;
+    constexpr int Q = (PSR + 31) / 32;
     float acc[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) acc[q] = 0.f;
@@ -774,7 +849,7 @@ __global__ void __launch_bounds__(256) seg_reduce_lane_kernel(const int64_t* __r
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
                 const int e = q * 32 + lane;
-                v[u][q] = (s + u < s1 && e < LANE_PS) ? part[(s + u) * (int64_t)LANE_PS + e] : 0.f;
+                v[u][q] = (s + u < s1 && e < PSR) ? part[(s + u) * (int64_t)PSR + e] : 0.f;
             }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
@@ -786,7 +861,7 @@ __global__ void __launch_bounds__(256) seg_reduce_lane_kernel(const int64_t* __r
     for (int q = 0; q < Q; ++q) {
         const int e = q * 32 + lane;
         if (e < nt) dst[e] = (double)acc[q];
-        else if (e >= LANE_NT && e < LANE_NT + r) dst[nt + (e - LANE_NT)] = (double)acc[q];
+        else if (e >= NTR && e < NTR + r) dst[nt + (e - NTR)] = (double)acc[q];
     }
 }
 
@@ -801,8 +876,13 @@ void launch_ls(int r, const Segments& sg, const int32_t* idx, const int64_t* pos
     if (sizeof(TG) == 4 && r <= LANE_R) {
         seg_gram_lane_kernel<TF, TV><<<smp::counted(g), 32 * LS_WARPS, 0, st>>>(sg.b, sg.e, sg.nseg, idx, pos, vals,
                                                                                 wt, sub, sid, Fin, r, (float*)part);
-        seg_reduce_lane_kernel<<<smp::counted(gr), 256, 0, st>>>(sg.start, (const float*)part, r, n_out, Gc);
+        seg_reduce_lane_kernel<LANE_R><<<smp::counted(gr), 256, 0, st>>>(sg.start, (const float*)part, r, n_out, Gc);
         solve_reg_kernel<TF, 12><<<smp::counted(gs), 32, 0, st>>>(Gc, r, n_out, Xout, err);
+    } else if (sizeof(TG) == 4 && r <= 20) {
+        seg_gram_lane2_kernel<TF, TV, 20, 14><<<smp::counted(g), 32 * LS_WARPS, 0, st>>>(
+            sg.b, sg.e, sg.nseg, idx, pos, vals, wt, sub, sid, Fin, r, (float*)part);
+        seg_reduce_lane_kernel<20><<<smp::counted(gr), 256, 0, st>>>(sg.start, (const float*)part, r, n_out, Gc);
+        solve_warp_kernel<TF><<<smp::counted(gw), 256, 0, st>>>(Gc, r, n_out, Xout, err);
     } else if (r <= 8) {
         seg_gram_kernel<TF, TG, TV, 8><<<smp::counted(g), 32 * LS_WARPS, 0, st>>>(sg.b, sg.e, sg.nseg, idx, pos,
                                                                                   vals, qhat, sub, sid, Fin, r, part);
@@ -860,7 +940,7 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
     add(n1 + n2 + 2, 4);                     // segment counts
     add(n1 + n2 + 4, 8);                     // segment starts
     add(4 * nseg_max, 8);                    // segment begins / ends
-    add(nseg_max * (int64_t)std::max(r * r + r, LANE_PS), sizeof(TG));   // LS partials
+    add(nseg_max * (int64_t)std::max(r * r + r, std::max(LANE_PS, LANE2_PS)), sizeof(TG));   // LS partials
     add(nnz, 4);                                        // binary32 weights 1 / q^
     add(nseg_max * (int64_t)b, sizeof(TY));             // SpMM segment partials
     add(nmax * (int64_t)(r * (r + 1) / 2 + r), 8);      // compact per-row systems
@@ -898,7 +978,7 @@ smp_status waltmin_typed(smp_ctx* c, const TV* vals, int r, int T, uint32_t flag
     rows_sg.start = ar.take<int64_t>(n1 + 1);
     cols_sg.start = ar.take<int64_t>(n2 + 1);
     int64_t* seg_be = ar.take<int64_t>(4 * nseg_max);
-    TG* lspart = ar.take<TG>(nseg_max * (int64_t)std::max(r * r + r, LANE_PS));
+    TG* lspart = ar.take<TG>(nseg_max * (int64_t)std::max(r * r + r, std::max(LANE_PS, LANE2_PS)));
     float* wt = ar.take<float>(nnz);
     TY* Yp = ar.take<TY>(nseg_max * (int64_t)b);
     double* Gc = ar.take<double>(nmax * (int64_t)(r * (r + 1) / 2 + r));
