@@ -379,26 +379,8 @@ def main():
     b16ops = engine == smp.SMP_ENGINE_TC_BF16
     tc_used = engine in (smp.SMP_ENGINE_TC, smp.SMP_ENGINE_TC_BF16) or (engine == smp.SMP_ENGINE_AUTO and tc_active(smp))
     srht = engine == smp.SMP_ENGINE_SRHT
-    if srht:
-        roof = {"bound": "hbm", "achieved": sk_bytes / sk_avg_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "peak_kind": "%s HBM copy" % peak_kind}
-    elif b16ops:
-        roof = {"bound": "tensor", "achieved": sk_flops / sk_avg_s / 1e12, "peak": peaks["bf16_tflops"],
-                "unit": "TFLOP/s", "peak_kind": "%s bf16 burst" % peak_kind}
-    elif tc_used and sk_flops / sk_bytes * peaks["hbm_gbs"] / 1e3 < peaks["bf16_tflops"] * (1.1 / 2.25):
-        # k / 2 flop per input byte below the TF32 ridge: the HBM stream is the roofline
-        roof = {"bound": "hbm", "achieved": sk_bytes / sk_avg_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "peak_kind": "%s HBM copy" % peak_kind}
-    elif tc_used:
-        tf32_peak = peaks["bf16_tflops"] * (1.1 / 2.25)
-        roof = {"bound": "tensor", "achieved": sk_flops / sk_avg_s / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
-                "peak_kind": "%s bf16 burst x nominal tf32/bf16 ratio 1.1/2.25" % peak_kind}
-    else:
-        clk_mhz = peaks.get("sm_max_mhz", 2070.0)
-        alu_peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": sk_flops / sk_avg_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
-                "peak_kind": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x %.0f MHz" % clk_mhz}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+    kind = "srht" if srht else "tc_bf16" if b16ops else "tc" if tc_used else "simt"
+    roof = sketch_roofline(kind, sk_bytes, sk_flops, sk_avg_s, peaks, peak_kind)
     roof["traffic"] = sketch_traffic(sum(sk_rows) / len(sk_rows), w) if tc_used and not b16ops else None
     roof["kernel"] = ("smp_sketch_accumulate: block SRHT (srht_fused_kernel)" if srht else
                       "smp_sketch_accumulate: sketch_tc_kernel<BF16 operands> (tcgen05 kind::f16), Pi of the next "
@@ -975,6 +957,33 @@ def run_batched(args, w, embed=False):
     if embed:
         return line
     print(json.dumps(line), flush=True)
+
+
+def sketch_roofline(kind, sk_bytes, sk_flops, sk_avg_s, peaks, peak_kind):
+    """The sketch kernel's roofline object: kind "srht" (HBM), "tc_bf16" (BF16 tensor peak), "tc" (the TF32 peak,
+    derived from the measured BF16 one, or HBM when the sketch's k / 2 flop per input byte is below the TF32 ridge),
+    "simt" (FP32 FMA issue rate). sk_bytes / sk_flops: algorithmic bytes / flops per launch; sk_avg_s: mean launch
+    time."""
+    tf32_peak = peaks["bf16_tflops"] * (1.1 / 2.25)
+    hbm = {"bound": "hbm", "achieved": sk_bytes / sk_avg_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "peak_kind": "%s HBM copy" % peak_kind}
+    if kind == "srht":
+        roof = hbm
+    elif kind == "tc_bf16":
+        roof = {"bound": "tensor", "achieved": sk_flops / sk_avg_s / 1e12, "peak": peaks["bf16_tflops"],
+                "unit": "TFLOP/s", "peak_kind": "%s bf16 burst" % peak_kind}
+    elif kind == "tc" and sk_flops / sk_bytes * peaks["hbm_gbs"] / 1e3 < tf32_peak:
+        roof = hbm
+    elif kind == "tc":
+        roof = {"bound": "tensor", "achieved": sk_flops / sk_avg_s / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
+                "peak_kind": "%s bf16 burst x nominal tf32/bf16 ratio 1.1/2.25" % peak_kind}
+    else:
+        clk_mhz = peaks.get("sm_max_mhz", 2070.0)
+        alu_peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": sk_flops / sk_avg_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                "peak_kind": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x %.0f MHz" % clk_mhz}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    return roof
 
 
 def sketch_traffic(rows_per_launch, w):
