@@ -377,7 +377,7 @@ def main():
     sk_flops = 2.0 * w["k"] * sum(sk_rows) * ntot / len(sk_rows)
     sk_avg_s = sum(sk_ms) / len(sk_ms) / 1e3
     b16ops = engine == smp.SMP_ENGINE_TC_BF16
-    tc_used = engine in (smp.SMP_ENGINE_TC, smp.SMP_ENGINE_TC_BF16) or (engine == smp.SMP_ENGINE_AUTO and tc_active(smp))
+    tc_used = engine in (smp.SMP_ENGINE_TC, smp.SMP_ENGINE_TC_BF16) or (engine == smp.SMP_ENGINE_AUTO and tc_active(w))
     srht = engine == smp.SMP_ENGINE_SRHT
     kind = "srht" if srht else "tc_bf16" if b16ops else "tc" if tc_used else "simt"
     roof = sketch_roofline(kind, sk_bytes, sk_flops, sk_avg_s, peaks, peak_kind)
@@ -1006,9 +1006,10 @@ def sketch_traffic(rows_per_launch, w):
     return float(kv["traffic_bytes"]) * rows_per_launch / float(kv["rows"])
 
 
-def tc_active(smp):
-    """AUTO runs the tensor-core engine for FP32 blocks with k <= 512 and 16-byte aligned rows (the bench's)."""
-    return True
+def tc_active(w):
+    """AUTO runs the tensor-core engine for binary32 blocks with k <= 512 and 16-byte aligned rows (n1, n2 multiples
+    of 4 here: the bench's blocks are whole rows of contiguous tensors)."""
+    return w["k"] <= 512 and w["n1"] % 4 == 0 and w["n2"] % 4 == 0
 
 
 def run_e2e(torch, smp, solver, A, B, w, m, rank, steps, stream, world, dev):

@@ -58,3 +58,8 @@ def test_sketch_traffic_applies_only_to_the_captured_source_and_width(tmp_path, 
     assert bench.sketch_traffic(200, {"k": 500, "n1": 2000, "n2": 2000}) == pytest.approx(2000.0)
     assert bench.sketch_traffic(200, {"k": 500, "n1": 2048, "n2": 2048}) is None        # another width
     assert bench.sketch_traffic(200, {"k": 40, "n1": 2048, "n2": 2048}) is None         # another source hash
+
+
+def test_auto_engine_is_the_tensor_core_one_for_the_bench_shapes():
+    assert bench.tc_active(bench.WORKLOADS["scale"]) and bench.tc_active(bench.WORKLOADS["block_batch"])
+    assert not bench.tc_active(dict(bench.WORKLOADS["scale"], k=1024))
